@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput of the feedforward decentralized precoding path on GB300.
+
+Workload (one rank): PD-WF precoding of the 20 MHz LTE-like slot with U = 16
+users, B = 256 antennas in C = 8 clusters of 32, 1200 subcarriers x K = 14
+OFDM symbols, 16-QAM, SNR 10 dB, i.i.d. Rayleigh channel, complex64.  One
+step is one dp_precode call over `--slots` such slots (default 8, so that a
+step's inputs, 331 MB, exceed the 129 MB L2 and every step streams from HBM).
+Metric: precoded subcarriers per second (each subcarrier carries K vectors).
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torchrun, one rank per GPU, each rank precoding its own slots (replicas:
+subcarriers are independent, no collective on the data path).
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="c2", U=16, B=256, C=8, n_sc=1200, K=14, qam=16, snr_db=10.0)
+KERNEL_SOURCES = ["paper_1804_10987_gb300/csrc/dp_fp32.cu",
+                  "paper_1804_10987_gb300/csrc/dp_blocks.cuh",
+                  "paper_1804_10987_gb300/csrc/dp_common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["wf", "zf", "fdwf"], default="wf")
+    ap.add_argument("--slots", type=int, default=8, help="slots of 1200 subcarriers per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="bound of the CPU oracle sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def metric_name(mode):
+    return f"precoded subcarriers/s ({mode.upper()}, U=16 B=256 C=8 K=14, complex64)"
+
+
+def config_dict(args, world, slots):
+    w = WORKLOAD
+    return {"workload": f"c2: U={w['U']} B={w['B']} C={w['C']}x32 n_sc={w['n_sc']}/slot "
+                        f"K={w['K']} {w['qam']}-QAM SNR {w['snr_db']:g} dB iid Rayleigh",
+            "mode": args.mode, "slots_per_step": slots,
+            "subcarriers_per_step": w["n_sc"] * slots,
+            "l2": "inputs larger than L2 (331 MB per step of 8 slots vs 129 MB L2)",
+            "parallelism": f"replicas x{world}"}
+
+
+# ----------------------------------------------------------------- clocks ----
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                 power=float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        loaded = [r for r in rows if r["power"] > 0.25 * max(x["power"] for x in rows)] or rows
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in loaded),
+                "sm_max_mhz": max(r["smax"] for r in rows), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ CPU oracle -----
+def make_slot_host(slot_index: int, mode: str):
+    from paper_1804_10987_gb300 import synth
+    w = WORKLOAD
+    return synth.make_problem(w["U"], w["B"], w["C"], w["n_sc"], w["K"], w["qam"], w["snr_db"],
+                              seed=synth.seed_for(2, 100 + slot_index), mode=mode)
+
+
+def cpu_oracle_rate(mode: str, seconds: float, steps=None):
+    """Time the FP64 oracle, as it stands, on the host cores: slots of 1200
+    subcarriers until `seconds` elapse (or `steps` slots).  Returns
+    (subcarriers/s, cores, sample description, per-step seconds)."""
+    import oracle
+    p = make_slot_host(0, mode)
+    cores = os.cpu_count() or 1
+    oracle.build()
+    per = []
+    t_end = time.perf_counter() + seconds
+    while True:
+        t0 = time.perf_counter()
+        oracle.precode(p.H, p.S, p.cluster_sizes, mode, rho2=p.rho2, N0=p.N0, Es=p.Es,
+                       tau=p.tau, nthreads=cores, outputs=("X",))
+        per.append(time.perf_counter() - t0)
+        if steps is not None and len(per) >= steps:
+            break
+        if steps is None and time.perf_counter() >= t_end:
+            break
+    rate = p.n_sc * len(per) / sum(per)
+    sample = (f"{len(per)} x one slot of {p.n_sc} subcarriers (U=16, B=256, K=14, {mode}), "
+              f"{cores} threads")
+    return rate, cores, sample, per
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    _, cores, _, _ = cpu_oracle_rate(args.mode, 0.0, steps=max(1, args.warmup))
+    rate, cores, sample, per = cpu_oracle_rate(args.mode, 0.0, steps=max(1, args.steps))
+    ms = 1e3 * sum(per) / len(per)
+    line = {"impl": "reference", "metric": metric_name(args.mode), "value": rate,
+            "unit": "subcarriers/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(config_dict(args, 1, 1), slots_per_step=1,
+                           subcarriers_per_step=WORKLOAD["n_sc"]),
+            "cpu_baseline": {"value": rate, "unit": "subcarriers/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": "subcarriers/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------- our arm ---------
+def sources_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(subcarriers_per_launch):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, scaled by subcarriers; None if missing or taken on other code."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("sources_hash") != sources_hash():
+        return None
+    return t["dram_bytes_per_subcarrier"] * subcarriers_per_launch
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def our_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1804_10987_gb300 import dp, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = WORKLOAD
+    slots = args.slots
+    n_sc = w["n_sc"] * slots
+    U, B, C, K = w["U"], w["B"], w["C"], w["K"]
+    N0 = synth.n0_from_snr(w["snr_db"])
+    stream = torch.cuda.current_stream()
+
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.seed_for(2, 500 + rank))
+    H = synth.torch_channel(n_sc, B, U, "iid", gen, "cuda")
+    S = synth.torch_symbols(w["qam"], (n_sc, K, U), gen, "cuda")
+    X = torch.empty((n_sc, K, B), dtype=torch.complex64, device="cuda")
+    plan = dp.Plan(U, B, C, n_sc, K, mode=args.mode, N0=N0, tau=0.125, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plan.precode(H, S, X)
+    st = plan.status_get()
+    assert (st == 0).all(), "precoding reported failures"
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus)
+    sampler.start()
+    torch.cuda.synchronize()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        plan.precode(H, S, X)
+        ev[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms_total = t0.elapsed_time(t1)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = n_sc * args.steps * world / (ms_total / 1e3)
+
+    # roofline of the fused kernel: algorithmic bytes = H once + S + X
+    alg_bytes = n_sc * (B * U * 8 + K * U * 8 + K * B * 8)
+    kern_s = statistics.mean(launch_ms) / 1e3
+    peak, peak_src = load_peaks()
+    achieved = alg_bytes / kern_s / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_fused<16>", "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_per_launch(n_sc), "algorithmic_bytes": alg_bytes,
+                "launch_ms_mean": kern_s * 1e3}
+
+    # end to end through the public call with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Hh = H.cpu().pin_memory()
+        Sh = S.cpu().pin_memory()
+        Xh = torch.empty(X.shape, dtype=X.dtype).pin_memory()
+        e_steps = max(3, min(args.steps, 10))
+        for _ in range(2):
+            H.copy_(Hh, non_blocking=True)
+            S.copy_(Sh, non_blocking=True)
+            plan.precode(H, S, X)
+            Xh.copy_(X, non_blocking=True)
+        torch.cuda.synchronize()
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(e_steps):
+            H.copy_(Hh, non_blocking=True)
+            S.copy_(Sh, non_blocking=True)
+            plan.precode(H, S, X)
+            Xh.copy_(X, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b)
+        if world > 1:
+            t = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": n_sc * e_steps * world / (e_ms / 1e3), "unit": "subcarriers/s",
+               "h2d_bytes_per_step": H.numel() * 8 + S.numel() * 8,
+               "d2h_bytes_per_step": X.numel() * 8, "steps": e_steps}
+        assert np.isfinite(Xh[:2].numpy()).all()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample, _ = cpu_oracle_rate(args.mode, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "subcarriers/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    plan.close()
+    if rank == 0:
+        line = {"metric": metric_name(args.mode), "value": value, "unit": "subcarriers/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 (complex64)", "data": "synthetic",
+                "config": config_dict(args, world, slots), "roofline": roofline,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "clocks": clocks,
+                "vectors_per_s": value * K,
+                "paper_context": "PD-WF U=16 B=256 C=8 on 8 V100 (one per cluster), K=7: "
+                                 "0.607 ms per 1200-subcarrier slot = 1.98 M subcarriers/s"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        our_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,154 @@
+/*
+ * dprecode.h -- C ABI of the GB300 (sm_103a) library for feedforward
+ * decentralized precoding in the massive MU-MIMO downlink
+ * (Li, Jeon, Cavallaro, Studer, arXiv:1804.10987).
+ *
+ * Problem (Sec. II-A, Sec. III-A): for every OFDM subcarrier n a base station
+ * with B antennas serves U single-antenna users over the U x B channel H_n,
+ * constant over K OFDM symbols.  The antennas are split into C clusters of
+ * B_c contiguous antennas, H = [H_1, ..., H_C].  Given symbol vectors
+ * s[k] in C^U the library computes the precoded vectors x[k] = [x_1; ...; x_C]
+ * in C^B:
+ *
+ *   DP_WF   centralized Wiener filter, computed the partially decentralized way
+ *           (PD-WF, Sec. III-B): G_c = H_c H_c^H, G = sum_c G_c,
+ *           A = G + kappa I with kappa = U N0 / rho^2 (Thm. 1),
+ *           scale = 1/beta = rho / sqrt(Es tr(A^{-1} G A^{-1})) (Thm. 1,
+ *           Lemma 1), z[k] = A^{-1} s[k], x_c[k] = scale H_c^H z[k].
+ *   DP_ZF   zero forcing: the same with kappa = 0 (needs B >= U).
+ *   DP_FDWF fully decentralized WF (Sec. III-D): every cluster runs its own WF
+ *           on (H_c, rho_c^2 = rho^2 / C) with kappa_c = tau U N0 / rho_c^2
+ *           (Eq. (16)): x_c[k] = scale_c H_c^H (G_c + kappa_c I)^{-1} s[k].
+ *
+ * Memory layouts (row-major; complex = interleaved float pair re, im, i.e.
+ * the paper's single-precision complex type; every array pointer is
+ * caller-owned DEVICE memory unless a parameter says "host"):
+ *   H     [n_sc][B][U]  complex  the U x B channel stored column-major, user
+ *                                index fastest; cluster c is the contiguous
+ *                                antenna block [off_c, off_c + B_c)
+ *   S     [n_sc][K][U]  complex  symbol vectors
+ *   X     [n_sc][K][B]  complex  precoded vectors
+ *   G     [n_sc][U][U]  complex  summed Gram (full Hermitian matrix)
+ *   Gloc  [C][n_sc][U][U]        per-cluster Grams
+ *   Z     WF/ZF [n_sc][K][U], FD [n_sc][C][K][U]   z = A^{-1} s (unscaled)
+ *   scale WF/ZF [n_sc],       FD [n_sc][C]         float, scale = 1 / beta
+ * All device pointers must be 16-byte aligned (cudaMalloc / torch allocations
+ * are).
+ *
+ * Execution: every compute call is asynchronous on the plan's stream and
+ * returns after enqueueing.  Argument errors are detected on the host and
+ * returned synchronously (nothing is enqueued).  Numerical failures of one
+ * subcarrier (a non-positive pivot, i.e. A not positive definite, or a
+ * non-finite input) never trap: the outputs of that subcarrier are zeroed and
+ * its entry of the plan's device status array is set; dp_status_get() reads
+ * it.  There is no CPU fallback: without a CUDA device every compute call
+ * returns DP_ERR_CUDA.
+ */
+#ifndef DPRECODE_H
+#define DPRECODE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DP_OK = 0,
+  DP_ERR_INVALID_ARG = 1,  /* NULL pointer, size out of range, bad enum */
+  DP_ERR_PARTITION = 2,    /* cluster sizes < 1 or not summing to B */
+  DP_ERR_UNSUPPORTED = 3,  /* valid but not implemented (e.g. ZF with B < U) */
+  DP_ERR_OOM = 4,          /* device allocation failed */
+  DP_ERR_CUDA = 5,         /* a CUDA runtime call failed / no device */
+  DP_ERR_NOT_PD = 6,       /* per subcarrier: A not positive definite */
+  DP_ERR_NONFINITE = 7,    /* per subcarrier: non-finite H or s */
+  DP_ERR_TIMEOUT = 8       /* a bounded on-device wait gave up */
+} dp_status;
+
+typedef enum { DP_ZF = 0, DP_WF = 1, DP_FDWF = 2 } dp_mode;
+
+/* Arithmetic of the Gram contraction G_c = H_c H_c^H (Sec. III-B):
+ * FP32 SIMT, or tensor cores (tcgen05) with BF16 / FP16 inputs and FP32
+ * accumulation.  The solve and the apply are FP32 in every case. */
+typedef enum { DP_FP32 = 0, DP_BF16 = 1, DP_FP16 = 2 } dp_precision;
+
+/* Stream handle; identical to cudaStream_t.  NULL = the legacy default
+ * stream. */
+typedef struct CUstream_st *dp_stream_t;
+
+typedef struct {
+  int U;                     /* users, 1 <= U <= 64 */
+  int B;                     /* antennas, U <= B for ZF, B <= 4096 */
+  int C;                     /* clusters, 1 <= C <= B */
+  const int *cluster_sizes;  /* host array of C sizes B_c >= 1 summing to B
+                                (contiguous antenna blocks in order), or NULL
+                                for C equal clusters (needs B % C == 0).
+                                Copied by dp_plan_create. */
+  int n_sc;                  /* subcarriers, >= 0 */
+  int K;                     /* OFDM symbols per subcarrier, 0 <= K <= 64 */
+  dp_mode mode;
+  dp_precision prec;
+  float rho2;                /* total transmit power rho^2 > 0 */
+  float N0;                  /* noise variance per entry >= 0 (WF, FD) */
+  float Es;                  /* symbol energy E|s_u|^2 > 0 (1 for normalized QAM) */
+  float tau;                 /* FD-WF tau_c >= 0 (Eq. (16)); ignored otherwise */
+  int refine;                /* 1: one step of iterative refinement of z after a
+                                reduced-precision Gram (FP64 residual); 0: none */
+} dp_plan_desc;
+
+typedef struct dp_plan *dp_plan_t;
+
+/* Validate the description, copy it, and allocate the plan's workspace (the
+ * cluster offsets and a device status array [n_sc]) on the current device.
+ * stream: where every call of this plan enqueues.  On error *out is NULL. */
+dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t *out);
+/* Free the plan and its workspace (synchronizes the plan's stream). */
+dp_status dp_plan_destroy(dp_plan_t plan);
+/* Change the stream later calls enqueue on. */
+dp_status dp_plan_set_stream(dp_plan_t plan, dp_stream_t stream);
+
+/* Step a1 (Sec. III-B, local Gram of every cluster):
+ * Gloc[c][n] = H_c H_c^H for all clusters c and subcarriers n. */
+dp_status dp_gram_local(dp_plan_t plan, const void *H, void *Gloc);
+
+/* Step a2 (Sec. III-B, feedforward adder tree; Fig. 1(a)):
+ * G[n] = sum_c Gloc[c][n], summed in cluster order. */
+dp_status dp_gram_reduce(dp_plan_t plan, const void *Gloc, void *G);
+
+/* Steps a3-a5 (Thm. 1, Lemma 1, Eq. (14); Sec. III-B whitening node;
+ * Sec. III-D for FD-WF): regularize, factor, precoding factor, whitening.
+ * WF/ZF: input G [n_sc][U][U]; A = G + kappa I; Z[n][k] = A^{-1} s[k];
+ *        scale[n] = rho / sqrt(Es tr(A^{-1} G A^{-1})).
+ * FD:    input Gloc [C][n_sc][U][U]; per cluster A_c = G_c + kappa_c I;
+ *        Z[n][c][k] = A_c^{-1} s[k]; scale[n][c] = rho_c / sqrt(Es t_c).
+ * For FD clusters with B_c < U the U x U system equals the paper's
+ * B_c x B_c form by the push-through identity when kappa_c > 0; with
+ * kappa_c = 0 such a cluster returns DP_ERR_UNSUPPORTED. */
+dp_status dp_solve(dp_plan_t plan, const void *G_or_Gloc, const void *S, void *Z, float *scale);
+
+/* Step a6 (Sec. III-B local precoding, with the normalization fused):
+ * X[n][k][b] = scale * sum_u conj(H[n][b][u]) Z[n][k][u] over each cluster's
+ * antennas, with the cluster's own Z and scale in FD mode. */
+dp_status dp_precode_apply(dp_plan_t plan, const void *H, const void *Z, const float *scale,
+                           void *X);
+
+/* Steps a1-a6 fused: X from H and S.  Reads H once from HBM for every size
+ * whose per-system antenna block fits in shared memory; the plan's
+ * precision selects the Gram arithmetic. */
+dp_status dp_precode(dp_plan_t plan, const void *H, const void *S, void *X);
+
+/* Wait for the plan's stream and copy the per-subcarrier status of the last
+ * call that wrote it into host_status[n_sc] (host memory; may be NULL).
+ * Returns the first non-DP_OK entry (DP_OK if all succeeded). */
+dp_status dp_status_get(dp_plan_t plan, int *host_status);
+
+/* Static description of a status code. */
+const char *dp_status_string(dp_status s);
+
+/* Library version string. */
+const char *dp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DPRECODE_H */

@@ -1,0 +1,284 @@
+// dp_blocks.cuh -- device building blocks of the FP32 precoding path.
+//
+// Shared-memory tile of one system's channel: rows = antennas b, each row the
+// U user entries H[b][0..U) as complex floats, padded to UP (a multiple of 8)
+// with zeros, row stride RS = 2 UP + 4 floats.  The 16-byte pad makes a
+// thread-per-row walk (the apply) hit distinct bank groups within every
+// quarter warp, while the Gram's same-row reads broadcast.
+#pragma once
+
+#include "dp_common.cuh"
+
+namespace dp {
+
+constexpr int NT = 256;  // threads per CTA of the per-system kernels
+
+constexpr int pow2_floor(int x) {
+  int p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
+
+template <int UP>
+struct Geo {
+  static_assert(UP % 8 == 0 && UP >= 8 && UP <= 64, "UP must be 8..64, a multiple of 8");
+  static constexpr int RS = 2 * UP + 4;
+  static constexpr int M = UP / 4;                 // 4 x 4 tiles per side of G
+  static constexpr int NTILES = M * (M + 1) / 2;   // lower-triangular tiles
+  static constexpr int NBG0 = pow2_floor(NT / NTILES);
+  // antenna groups per tile: a power of two <= 32 so that a group is a
+  // lane-aligned slice of one warp and reduces with xor shuffles
+  static constexpr int NBG = NBG0 > 32 ? 32 : (NBG0 < 1 ? 1 : NBG0);
+  static_assert(NTILES * NBG <= NT, "one Gram item per thread");
+};
+
+// ------------------------------------------------------------ row fetch ---
+// Fetch rows [lo, lo + nrows) of one subcarrier's channel Hn (rows of U
+// complex) into the padded tile Hs.  With tma, warp 0 posts the byte count on
+// bar and issues one 1-D bulk copy per row (the caller waits on bar);
+// otherwise all threads copy with plain loads (the caller syncs).
+template <int UP>
+__device__ __forceinline__ void fetch_rows(float *Hs, const float2 *__restrict__ Hn, int lo,
+                                           int nrows, int U, bool tma, uint64_t *bar, int tid) {
+  constexpr int RS = Geo<UP>::RS;
+  if (tma) {
+    if (tid < 32) {
+      if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)nrows * (uint32_t)U * 8u);
+      __syncwarp();
+      for (int r = tid; r < nrows; r += 32)
+        tma_load_1d(Hs + r * RS, Hn + (size_t)(lo + r) * U, (uint32_t)U * 8u, bar);
+    }
+  } else {
+    for (int e = tid; e < nrows * U; e += NT) {
+      int r = e / U, u = e - r * U;
+      float2 v = __ldg(Hn + (size_t)(lo + r) * U + u);
+      *reinterpret_cast<float2 *>(Hs + r * RS + 2 * u) = v;
+    }
+  }
+}
+
+// Zero the pad columns [U, UP) of rows [0, nrows) (once per buffer: bulk
+// copies write only the first U entries of a row).
+template <int UP>
+__device__ __forceinline__ void zero_row_pads(float *Hs, int nrows, int U, int tid) {
+  constexpr int RS = Geo<UP>::RS;
+  const int w = RS - 2 * U;
+  for (int e = tid; e < nrows * w; e += NT) {
+    int r = e / w, c = e - r * w;
+    Hs[r * RS + 2 * U + c] = 0.f;
+  }
+}
+
+// ------------------------------------------------------------------ Gram ---
+// G = sum over the tile's rows of h_b h_b^H (h_b = row b), accumulated by
+// 4 x 4 register tiles of the lower triangle; each tile is split over NBG
+// antenna groups (rows b = bg mod NBG), reduced with xor shuffles at the end.
+template <int UP>
+struct GramAcc {
+  float2 acc[4][4];
+  int ti, tj, bg;
+  bool active;
+
+  __device__ __forceinline__ void init(int tid) {
+    constexpr int NB = Geo<UP>::NBG, NTL = Geo<UP>::NTILES;
+    active = tid < NTL * NB;
+    int tile = tid / NB;
+    bg = tid % NB;
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= tile) ++i;
+    ti = i;
+    tj = tile - i * (i + 1) / 2;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = make_float2(0.f, 0.f);
+  }
+
+  // Rows [0, nrows) of Hs; nrows may vary between calls (chunks), the group
+  // assignment restarts at row 0 of every chunk.
+  __device__ __forceinline__ void accumulate(const float *Hs, int nrows) {
+    constexpr int NB = Geo<UP>::NBG, RS = Geo<UP>::RS;
+    if (!active) return;
+    for (int r = bg; r < nrows; r += NB) {
+      const float4 *row = reinterpret_cast<const float4 *>(Hs + r * RS);
+      float4 a0 = row[2 * ti], a1 = row[2 * ti + 1];
+      float4 b0 = row[2 * tj], b1 = row[2 * tj + 1];
+      float2 a[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                     make_float2(a1.z, a1.w)};
+      float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                     make_float2(b1.z, b1.w)};
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cmac_cj(acc[p][q], b[q], a[p]);  // += a_p conj(b_q)
+    }
+  }
+
+  // Reduce over the antenna groups and store the tile and its Hermitian
+  // mirror into G [UP][UP] (shared).  Every thread of the CTA must call it.
+  __device__ __forceinline__ void finish(float2 *G, int tid) {
+    constexpr int NB = Geo<UP>::NBG;
+    if (!active) return;
+    const int lane = tid & 31;
+    const unsigned mask = (NB == 32) ? FULL : (((1u << NB) - 1u) << (lane & ~(NB - 1)));
+#pragma unroll
+    for (int o = NB / 2; o >= 1; o >>= 1)
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          acc[p][q].x += __shfl_xor_sync(mask, acc[p][q].x, o);
+          acc[p][q].y += __shfl_xor_sync(mask, acc[p][q].y, o);
+        }
+    if (bg != 0) return;
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = 4 * ti + p, j = 4 * tj + q;
+        if (ti == tj && q > p) continue;
+        float2 v = acc[p][q];
+        if (i == j) v.y = 0.f;
+        G[i * UP + j] = v;
+        G[j * UP + i] = cconj(v);
+      }
+  }
+};
+
+// ------------------------------------------------------------ reductions ---
+// Deterministic CTA sum (fixed shuffle tree, then warps in order).
+__device__ __forceinline__ float cta_sum(float v, float *red, int tid) {
+  v = warp_sum(v);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  float s = 0.f;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------- CTA-wide inversion ------
+// In-place Gauss-Jordan inversion of the Hermitian positive definite A
+// [UP][UP] (leading U x U block), no pivoting: for a positive definite matrix
+// the pivots are the LDL^H pivots and stay positive.  Returns ST_OK or
+// ST_NOT_PD on a pivot that is not a positive finite number.  Caller has
+// synced after writing A.
+template <int UP>
+__device__ int cta_gj_inverse(float2 *A, int U, int tid) {
+  for (int p = 0; p < U; ++p) {
+    const float piv = A[p * UP + p].x;
+    if (!(piv > 0.f) || !isfinite(piv)) return ST_NOT_PD;  // uniform over the CTA
+    const float ip = 1.f / piv;
+    for (int e = tid; e < U * UP; e += NT) {
+      const int i = e / UP, j = e - i * UP;
+      if (j < U && i != p && j != p) {
+        float2 f = cscale(A[i * UP + p], ip);
+        cmsub(A[i * UP + j], f, A[p * UP + j]);
+      }
+    }
+    __syncthreads();
+    if (tid < U) {
+      if (tid != p) A[p * UP + tid] = cscale(A[p * UP + tid], ip);
+    } else if (tid < 2 * U) {
+      const int i = tid - U;
+      if (i != p) A[i * UP + p] = cscale(A[i * UP + p], -ip);
+    } else if (tid == 2 * U) {
+      A[p * UP + p] = make_float2(ip, 0.f);
+    }
+    __syncthreads();
+  }
+  return ST_OK;
+}
+
+// t = tr(T G T) = sum_ij (T G)_ij conj(T_ij) with T = A^{-1}: the definition
+// tr(Q^H Q) of Thm. 1 through Eq. (14), free of the cancellation of the
+// Lemma 1 difference tr(T) - kappa ||T||_F^2 when kappa dominates G.
+template <int UP>
+__device__ float cta_trace_tgt(const float2 *T, const float2 *G, int U, float *red, int tid) {
+  float part = 0.f;
+  for (int e = tid; e < U * UP; e += NT) {
+    const int i = e / UP, j = e - i * UP;
+    if (j < U) {
+      float2 acc = make_float2(0.f, 0.f);
+      for (int k = 0; k < U; ++k) cmac(acc, T[i * UP + k], G[k * UP + j]);
+      const float2 t = T[i * UP + j];
+      part = fmaf(acc.x, t.x, fmaf(acc.y, t.y, part));
+    }
+  }
+  return cta_sum(part, red, tid);
+}
+
+// Zs[k][i] = sum_j T_ij s[k][j] for k < K, i < U (T Hermitian: T_ij =
+// conj(T_ji), read along the row the lanes walk).
+template <int UP>
+__device__ void cta_whiten(const float2 *T, const float2 *Ss, float2 *Zs, int U, int K, int tid) {
+  for (int e = tid; e < K * UP; e += NT) {
+    const int k = e / UP, i = e - k * UP;
+    float2 acc = make_float2(0.f, 0.f);
+    if (i < U)
+      for (int j = 0; j < U; ++j) cmac_cj(acc, T[j * UP + i], Ss[k * UP + j]);
+    Zs[k * UP + i] = acc;
+  }
+}
+
+// ----------------------------------------------------------------- apply ---
+// X[k][lo + r] = scale * sum_u conj(H[r][u]) z[k][u] for the tile rows r <
+// nrows; z from shared Zs [K][UP] (pad entries zero).  Thread per row, rows
+// tid + j NT; K in blocks of KB accumulators.  Stores are coalesced along b.
+template <int UP, int KB>
+__device__ void apply_rows(const float *Hs, int nrows, const float2 *Zs, int K, float scale,
+                           float2 *__restrict__ Xn, int B, int lo, int tid) {
+  constexpr int RS = Geo<UP>::RS;
+  for (int r = tid; r < nrows; r += NT) {
+    const float *hrow = Hs + r * RS;
+    for (int kb = 0; kb < K; kb += KB) {
+      float2 acc[KB];
+#pragma unroll
+      for (int kk = 0; kk < KB; ++kk) acc[kk] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < UP; u += 2) {
+        const float4 h = *reinterpret_cast<const float4 *>(hrow + 2 * u);
+        const float2 h0 = make_float2(h.x, h.y), h1 = make_float2(h.z, h.w);
+#pragma unroll
+        for (int kk = 0; kk < KB; ++kk) {
+          if (kb + kk < K) {
+            const float4 z = *reinterpret_cast<const float4 *>(Zs + (kb + kk) * UP + u);
+            cmac_cj(acc[kk], h0, make_float2(z.x, z.y));
+            cmac_cj(acc[kk], h1, make_float2(z.z, z.w));
+          }
+        }
+      }
+#pragma unroll
+      for (int kk = 0; kk < KB; ++kk)
+        if (kb + kk < K) Xn[(size_t)(kb + kk) * B + lo + r] = cscale(acc[kk], scale);
+    }
+  }
+}
+
+template <int UP>
+__device__ void zero_rows(int nrows, int K, float2 *__restrict__ Xn, int B, int lo, int tid) {
+  for (int e = tid; e < nrows * K; e += NT) {
+    const int k = e / nrows, r = e - k * nrows;
+    Xn[(size_t)k * B + lo + r] = make_float2(0.f, 0.f);
+  }
+}
+
+// Load S_n [K][U] into Ss [K][UP] (zero pads); returns (via the CTA vote)
+// whether every entry is finite.
+template <int UP>
+__device__ bool load_symbols(const float2 *__restrict__ Sn, float2 *Ss, int U, int K, int tid) {
+  bool fin = true;
+  for (int e = tid; e < K * UP; e += NT) {
+    const int k = e / UP, u = e - k * UP;
+    float2 v = make_float2(0.f, 0.f);
+    if (u < U) {
+      v = __ldg(Sn + (size_t)k * U + u);
+      fin = fin && cfinite(v);
+    }
+    Ss[e] = v;
+  }
+  return __syncthreads_and(fin) != 0;
+}
+
+}  // namespace dp

@@ -1,0 +1,31 @@
+// dp_internal.h -- host-side declarations shared by the C ABI and the kernel
+// translation units (not part of the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "dp_common.cuh"
+
+namespace dp {
+
+// Users padded to the kernels' granularity (a multiple of 8, at most 64).
+inline int padded_users(int U) { return ((U + 7) / 8) * 8; }
+
+// Antenna rows per shared-memory chunk of the streaming Gram / apply kernels.
+int stream_chunk_rows(int UP);
+
+// Dynamic shared memory of the fused kernel for systems of up to maxrows
+// antennas; 0 if it cannot fit in one CTA.
+size_t fused_smem_bytes(int UP, int maxrows, int K);
+
+cudaError_t launch_gram(const SysDesc &d, int UP, const float2 *H, float2 *Gout,
+                        cudaStream_t s);
+cudaError_t launch_reduce(const float2 *Gloc, float2 *G, int C, size_t per, cudaStream_t s);
+cudaError_t launch_solve(const SysDesc &d, int UP, const float2 *Gin, const float2 *S, float2 *Z,
+                         float *scale, int *status, cudaStream_t s);
+cudaError_t launch_apply(const SysDesc &d, int UP, const float2 *H, const float2 *Z,
+                         const float *scale, float2 *X, cudaStream_t s);
+cudaError_t launch_fused(const SysDesc &d, int UP, int maxrows, const float2 *H, const float2 *S,
+                         float2 *X, int *status, float *scale_out, cudaStream_t s);
+
+}  // namespace dp

@@ -1,0 +1,219 @@
+"""Thin Python binding of the C ABI in include/dprecode.h (argument marshalling
+only: every step of the precoding path runs in the CUDA library).
+
+Tensors are torch CUDA tensors, complex64 (or float32 for ``scale``), C-
+contiguous, in the layouts the header states:
+  H [n_sc][B][U], S [n_sc][K][U], X [n_sc][K][B], G [n_sc][U][U],
+  Gloc [C][n_sc][U][U], Z [n_sc][K][U] (FD: [n_sc][C][K][U]),
+  scale [n_sc] (FD: [n_sc][C]).
+Calls enqueue on the plan's stream (by default torch's current stream at plan
+creation) and return immediately.  There is no fallback: if the library is
+missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, INVALID_ARG, PARTITION, UNSUPPORTED, OOM, CUDA, NOT_PD, NONFINITE, TIMEOUT = range(9)
+MODES = {"zf": 0, "wf": 1, "fdwf": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DPError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+        self.code = code
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("U", ctypes.c_int), ("B", ctypes.c_int), ("C", ctypes.c_int),
+                ("cluster_sizes", ctypes.POINTER(ctypes.c_int)),
+                ("n_sc", ctypes.c_int), ("K", ctypes.c_int),
+                ("mode", ctypes.c_int), ("prec", ctypes.c_int),
+                ("rho2", ctypes.c_float), ("N0", ctypes.c_float), ("Es", ctypes.c_float),
+                ("tau", ctypes.c_float), ("refine", ctypes.c_int)]
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libdprecode.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run paper_1804_10987_gb300.build")
+        L = ctypes.CDLL(path)
+        P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+        L.dp_plan_create.argtypes = [ctypes.POINTER(PlanDesc), P, ctypes.POINTER(P)]
+        L.dp_plan_destroy.argtypes = [P]
+        L.dp_plan_set_stream.argtypes = [P, P]
+        L.dp_gram_local.argtypes = [P, P, P]
+        L.dp_gram_reduce.argtypes = [P, P, P]
+        L.dp_solve.argtypes = [P, P, P, P, P]
+        L.dp_precode_apply.argtypes = [P, P, P, P, P]
+        L.dp_precode.argtypes = [P, P, P, P]
+        L.dp_status_get.argtypes = [P, P]
+        L.dp_status_string.argtypes = [I]
+        L.dp_status_string.restype = ctypes.c_char_p
+        L.dp_version.restype = ctypes.c_char_p
+        for name in ("dp_plan_create", "dp_plan_destroy", "dp_plan_set_stream", "dp_gram_local",
+                     "dp_gram_reduce", "dp_solve", "dp_precode_apply", "dp_precode",
+                     "dp_status_get"):
+            getattr(L, name).restype = I
+        _ = (F,)
+        _lib = L
+        return L
+
+
+def status_string(code: int) -> str:
+    return load().dp_status_string(int(code)).decode()
+
+
+def _check(code: int, what: str):
+    if code != OK:
+        raise DPError(code, what)
+
+
+def _ptr(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A precoding plan (dp_plan_t): problem sizes, cluster partition, mode,
+    precision and power / noise parameters; owns the device workspace."""
+
+    def __init__(self, U: int, B: int, C: int, n_sc: int, K: int, mode: str = "wf",
+                 prec: str = "fp32", rho2: float = 1.0, N0: float = 0.1, Es: float = 1.0,
+                 tau: float = 0.125, refine: int = 0, cluster_sizes=None, stream=None):
+        import torch
+        self.U, self.B, self.C, self.n_sc, self.K = int(U), int(B), int(C), int(n_sc), int(K)
+        self.mode, self.prec = mode, prec
+        self.rho2, self.N0, self.Es, self.tau, self.refine = rho2, N0, Es, tau, refine
+        self.cluster_sizes = None if cluster_sizes is None else [int(c) for c in cluster_sizes]
+        self._lib = load()
+        self._cs = None
+        cs_ptr = None
+        if self.cluster_sizes is not None:
+            self._cs = (ctypes.c_int * len(self.cluster_sizes))(*self.cluster_sizes)
+            cs_ptr = ctypes.cast(self._cs, ctypes.POINTER(ctypes.c_int))
+        if mode not in MODES or prec not in PRECISIONS:
+            raise ValueError(f"mode {mode!r} / precision {prec!r} unknown")
+        d = PlanDesc(self.U, self.B, self.C, cs_ptr, self.n_sc, self.K, MODES[mode],
+                     PRECISIONS[prec], rho2, N0, Es, tau, int(refine))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        handle = ctypes.c_void_p()
+        _check(self._lib.dp_plan_create(ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream),
+                                        ctypes.byref(handle)), "dp_plan_create")
+        self._h = handle
+
+    @property
+    def nsys(self) -> int:
+        return self.C if self.mode == "fdwf" else 1
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_stream(self, stream):
+        self._stream = stream
+        _check(self._lib.dp_plan_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)),
+               "dp_plan_set_stream")
+
+    # -- shapes -------------------------------------------------------------------
+    def shapes(self) -> dict:
+        n, U, B, C, K = self.n_sc, self.U, self.B, self.C, self.K
+        fd = self.mode == "fdwf"
+        return dict(H=(n, B, U), S=(n, K, U), X=(n, K, B), G=(n, U, U), Gloc=(C, n, U, U),
+                    Z=(n, C, K, U) if fd else (n, K, U), scale=(n, C) if fd else (n,))
+
+    # -- the C entry points ----------------------------------------------------------
+    def gram_local(self, H, Gloc):
+        import torch
+        s = self.shapes()
+        _check(self._lib.dp_gram_local(self._h, _ptr(H, torch.complex64, s["H"], "H"),
+                                       _ptr(Gloc, torch.complex64, s["Gloc"], "Gloc")),
+               "dp_gram_local")
+
+    def gram_reduce(self, Gloc, G):
+        import torch
+        s = self.shapes()
+        _check(self._lib.dp_gram_reduce(self._h, _ptr(Gloc, torch.complex64, s["Gloc"], "Gloc"),
+                                        _ptr(G, torch.complex64, s["G"], "G")), "dp_gram_reduce")
+
+    def solve(self, G_or_Gloc, S, Z, scale):
+        import torch
+        s = self.shapes()
+        gshape = s["Gloc"] if self.mode == "fdwf" else s["G"]
+        _check(self._lib.dp_solve(self._h, _ptr(G_or_Gloc, torch.complex64, gshape, "G"),
+                                  _ptr(S, torch.complex64, s["S"], "S"),
+                                  _ptr(Z, torch.complex64, s["Z"], "Z"),
+                                  _ptr(scale, torch.float32, s["scale"], "scale")), "dp_solve")
+
+    def precode_apply(self, H, Z, scale, X):
+        import torch
+        s = self.shapes()
+        _check(self._lib.dp_precode_apply(self._h, _ptr(H, torch.complex64, s["H"], "H"),
+                                          _ptr(Z, torch.complex64, s["Z"], "Z"),
+                                          _ptr(scale, torch.float32, s["scale"], "scale"),
+                                          _ptr(X, torch.complex64, s["X"], "X")),
+               "dp_precode_apply")
+
+    def precode(self, H, S, X):
+        import torch
+        s = self.shapes()
+        _check(self._lib.dp_precode(self._h, _ptr(H, torch.complex64, s["H"], "H"),
+                                    _ptr(S, torch.complex64, s["S"], "S"),
+                                    _ptr(X, torch.complex64, s["X"], "X")), "dp_precode")
+
+    def status_get(self) -> np.ndarray:
+        out = np.zeros(max(self.n_sc, 1), np.int32)
+        self._lib.dp_status_get(self._h, out.ctypes.data_as(ctypes.c_void_p))
+        return out[: self.n_sc]
+
+    # -- conveniences -------------------------------------------------------------
+    def empty(self, name: str):
+        import torch
+        dt = torch.float32 if name == "scale" else torch.complex64
+        return torch.empty(self.shapes()[name], dtype=dt, device="cuda")

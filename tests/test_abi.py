@@ -1,0 +1,87 @@
+"""The C-ABI library builds, loads and exports every function the public
+header declares; host-side argument validation (no device work).  CPU only."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1804_10987_gb300 import dp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", fn)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        for m in re.finditer(r"\b(dp_\w+)\s*\(", txt):
+            names.append(m.group(1))
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dp_plan_create", "dp_plan_destroy", "dp_gram_local", "dp_gram_reduce",
+                     "dp_solve", "dp_precode_apply", "dp_precode", "dp_status_get",
+                     "dp_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = dp.load()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    assert dp.status_string(dp.OK) == "ok"
+    assert "positive definite" in dp.status_string(dp.NOT_PD)
+    assert dp.load().dp_version().decode().startswith("dprecode")
+
+
+def _create(**kw):
+    lib = dp.load()
+    base = dict(U=8, B=64, C=2, cs=None, n_sc=4, K=2, mode=1, prec=0, rho2=1.0, N0=0.1, Es=1.0,
+                tau=0.125, refine=0)
+    base.update(kw)
+    cs = base.pop("cs")
+    arr = None
+    if cs is not None:
+        arr = (ctypes.c_int * len(cs))(*cs)
+    d = dp.PlanDesc(base["U"], base["B"], base["C"],
+                    ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)) if arr else None,
+                    base["n_sc"], base["K"], base["mode"], base["prec"], base["rho2"],
+                    base["N0"], base["Es"], base["tau"], base["refine"])
+    h = ctypes.c_void_p()
+    rc = lib.dp_plan_create(ctypes.byref(d), None, ctypes.byref(h))
+    if rc == dp.OK:
+        lib.dp_plan_destroy(h)
+    return rc
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(U=0), dp.INVALID_ARG), (dict(U=65), dp.INVALID_ARG), (dict(B=0), dp.INVALID_ARG),
+    (dict(C=0), dp.INVALID_ARG), (dict(C=65, B=64), dp.INVALID_ARG),
+    (dict(n_sc=-1), dp.INVALID_ARG), (dict(K=65), dp.INVALID_ARG), (dict(mode=7), dp.INVALID_ARG),
+    (dict(prec=9), dp.INVALID_ARG), (dict(rho2=0.0), dp.INVALID_ARG),
+    (dict(N0=-1.0), dp.INVALID_ARG), (dict(Es=float("nan")), dp.INVALID_ARG),
+    (dict(refine=2), dp.INVALID_ARG),
+    (dict(C=3), dp.PARTITION), (dict(C=2, cs=[30, 30]), dp.PARTITION),
+    (dict(C=2, cs=[64, 0]), dp.PARTITION),
+    (dict(mode=0, U=8, B=6, C=1), dp.UNSUPPORTED),
+    (dict(mode=2, N0=0.0, U=8, B=12, C=2), dp.UNSUPPORTED),
+])
+def test_plan_validation_on_host(kw, code):
+    assert _create(**kw) == code
+
+
+def test_null_arguments():
+    lib = dp.load()
+    assert lib.dp_plan_create(None, None, None) == dp.INVALID_ARG
+    assert lib.dp_precode(None, None, None, None) == dp.INVALID_ARG
+    assert lib.dp_status_get(None, None) == dp.INVALID_ARG
