@@ -142,6 +142,34 @@ dp_status dp_precode(dp_plan_t plan, const void *H, const void *S, void *X);
  * Returns the first non-DP_OK entry (DP_OK if all succeeded). */
 dp_status dp_status_get(dp_plan_t plan, int *host_status);
 
+/* Allocation-free precoding (the paper has no counterpart: this is a
+ * deployment variant of dp_precode).  For callers that cannot call
+ * cudaMalloc: a baseband runtime whose device memory is carved up once at
+ * start-up, a real-time slot loop where an allocation's latency or implicit
+ * synchronization would break the slot deadline, or code that runs while
+ * the caller's allocator is locked.  It runs the streaming form of
+ * dp_precode (Gram with the cluster sum, solve, apply; FP32) with all of its
+ * workspace in one static device array of DP_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library reserves until the process exits.  No plan is
+ * needed and nothing is allocated: the caller passes the description (as for
+ * dp_plan_create; prec must be DP_FP32, refine 0), the stream, and the device
+ * arrays H [n_sc][B][U], S [n_sc][K][U], X [n_sc][K][B] in the layouts above.
+ * The workspace needs, rounding each part up to 256 bytes,
+ *   4 (C + 1) + 4 n_sys + 8 n_sys U^2 + 8 n_sys K U + 4 n_sys  bytes,
+ * n_sys = n_sc (WF/ZF) or n_sc C (FD-WF); a larger problem returns
+ * DP_ERR_UNSUPPORTED before anything is enqueued.
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the array and each call
+ * overwrites what it reads, so calls whose work overlaps on the GPU race:
+ * serialize them (one stream, or events).  host_status: NULL to return after
+ * enqueueing; otherwise the call waits for the stream and writes the
+ * per-subcarrier status codes into host_status[n_sc] (host memory) and
+ * returns the first failure, as dp_status_get does. */
+#define DP_NOALLOC_SCRATCH_BYTES (8u << 20)
+dp_status dp_precode_noalloc(const dp_plan_desc *desc, dp_stream_t stream, const void *H,
+                             const void *S, void *X, int *host_status);
+
 /* Static description of a status code. */
 const char *dp_status_string(dp_status s);
 
