@@ -128,7 +128,9 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
     return DP_ERR_INVALID_ARG;
   if (d.refine != 0 && d.refine != 1) return DP_ERR_INVALID_ARG;
-  if (d.prec != DP_FP32) return DP_ERR_UNSUPPORTED;
+  // The tensor-core Gram covers up to 32 users; refinement is not built.
+  if (d.prec != DP_FP32 && !dp::tc_supported(dp::padded_users(d.U))) return DP_ERR_UNSUPPORTED;
+  if (d.refine != 0) return DP_ERR_UNSUPPORTED;
 
   std::vector<int> sizes(d.C);
   if (d.cluster_sizes) {
@@ -270,6 +272,9 @@ dp_status dp_precode(dp_plan_t p, const void *H, const void *S, void *X) {
   const float2 *sy = static_cast<const float2 *>(S);
   float2 *x = static_cast<float2 *>(X);
   cudaError_t e;
+  if (p->d.prec != DP_FP32)
+    return cuda_status(dp::launch_fused_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, p->d_status,
+                                           nullptr, p->stream));
   if (p->fused_fits)
     return cuda_status(
         dp::launch_fused(sd, p->UP, p->maxrows_sys, h, sy, x, p->d_status, nullptr, p->stream));

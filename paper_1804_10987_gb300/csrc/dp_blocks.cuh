@@ -281,4 +281,79 @@ __device__ bool load_symbols(const float2 *__restrict__ Sn, float2 *Ss, int U, i
   return __syncthreads_and(fin) != 0;
 }
 
+// ----------------------------------------------------- warp-per-system solve ---
+// Lane i holds row i of A = G + kappa I (UP complex registers).  In-place
+// Gauss-Jordan without pivoting (A Hermitian positive definite: the pivots are
+// the LDL^H pivots), row p broadcast by shuffles.  Leaves T = A^{-1}.
+template <int UP>
+__device__ __forceinline__ bool warp_gj_inverse(float2 (&row)[UP], int lane, int U) {
+#pragma unroll
+  for (int p = 0; p < UP; ++p) {
+    if (p >= U) break;
+    const float piv = __shfl_sync(FULL, row[p].x, p);
+    if (!(piv > 0.f) || !isfinite(piv)) return false;
+    const float ip = 1.f / piv;
+    const float2 f = cscale(row[p], ip);
+#pragma unroll
+    for (int j = 0; j < UP; ++j) {
+      float2 rp;
+      rp.x = __shfl_sync(FULL, row[j].x, p);
+      rp.y = __shfl_sync(FULL, row[j].y, p);
+      if (lane == p) {
+        row[j] = (j == p) ? make_float2(ip, 0.f) : cscale(rp, ip);
+      } else if (j == p) {
+        row[j] = make_float2(-f.x, -f.y);
+      } else {
+        cmsub(row[j], f, rp);
+      }
+    }
+  }
+  return true;
+}
+
+// One system solved by one warp (steps a3-a5): lane i holds row i of
+// A = G + kappa I; Gauss-Jordan inverse in registers, t = tr(T G T), scale =
+// sqrt(rho2 / (Es t)), z_k = T s_k written to zout[k * ldz + i] (i < U).
+// Gs [UP][UP] and Ss [K][UP] in shared memory with zero pads.  Returns the
+// status; on failure z = 0 and scale = 0.
+template <int UP>
+__device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int ldz, float kappa,
+                          float rho2, float Es, int U, int K, int lane, bool finite_in,
+                          float &scale) {
+  float2 row[UP];
+#pragma unroll
+  for (int j = 0; j < UP; ++j) {
+    row[j] = (lane < U) ? Gs[lane * UP + j] : make_float2(0.f, 0.f);
+    if (j == lane) row[j].x += kappa;
+  }
+  int st = finite_in ? ST_OK : ST_NONFINITE;
+  if (st == ST_OK && !warp_gj_inverse<UP>(row, lane, U)) st = ST_NOT_PD;
+  float sc = 0.f;
+  if (st == ST_OK) {
+    // t = sum_ij (T G)_ij conj(T_ij): lane i forms row i of T G
+    float part = 0.f;
+#pragma unroll
+    for (int j = 0; j < UP; ++j) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < UP; ++k) cmac(acc, row[k], Gs[k * UP + j]);
+      part = fmaf(acc.x, row[j].x, fmaf(acc.y, row[j].y, part));
+    }
+    if (lane >= U) part = 0.f;
+    const float t = warp_sum(part);
+    if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
+    else sc = sqrtf(rho2 / (Es * t));
+  }
+  for (int k = 0; k < K; ++k) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (st == ST_OK) {
+#pragma unroll
+      for (int j = 0; j < UP; ++j) cmac(acc, row[j], Ss[k * UP + j]);
+    }
+    if (lane < U) zout[(size_t)k * ldz + lane] = acc;
+  }
+  scale = sc;
+  return st;
+}
+
 }  // namespace dp

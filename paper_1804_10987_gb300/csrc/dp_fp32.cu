@@ -91,36 +91,6 @@ __global__ void k_reduce(const float2 *__restrict__ Gloc, float2 *__restrict__ G
   }
 }
 
-// ----------------------------------------------------- warp-per-system solve ---
-// Lane i holds row i of A = G + kappa I (UP complex registers).  In-place
-// Gauss-Jordan without pivoting (A Hermitian positive definite: the pivots are
-// the LDL^H pivots), row p broadcast by shuffles.  Leaves T = A^{-1}.
-template <int UP>
-__device__ __forceinline__ bool warp_gj_inverse(float2 (&row)[UP], int lane, int U) {
-#pragma unroll
-  for (int p = 0; p < UP; ++p) {
-    if (p >= U) break;
-    const float piv = __shfl_sync(FULL, row[p].x, p);
-    if (!(piv > 0.f) || !isfinite(piv)) return false;
-    const float ip = 1.f / piv;
-    const float2 f = cscale(row[p], ip);
-#pragma unroll
-    for (int j = 0; j < UP; ++j) {
-      float2 rp;
-      rp.x = __shfl_sync(FULL, row[j].x, p);
-      rp.y = __shfl_sync(FULL, row[j].y, p);
-      if (lane == p) {
-        row[j] = (j == p) ? make_float2(ip, 0.f) : cscale(rp, ip);
-      } else if (j == p) {
-        row[j] = make_float2(-f.x, -f.y);
-      } else {
-        cmsub(row[j], f, rp);
-      }
-    }
-  }
-  return true;
-}
-
 template <int UP>
 __global__ void __launch_bounds__(NT) k_solve_warp(SysDesc d, const float2 *__restrict__ Gin,
                                                    const float2 *__restrict__ S,
@@ -162,39 +132,9 @@ __global__ void __launch_bounds__(NT) k_solve_warp(SysDesc d, const float2 *__re
   fin = __all_sync(FULL, fin);
   __syncwarp();
 
-  float2 row[UP];
-#pragma unroll
-  for (int j = 0; j < UP; ++j) {
-    row[j] = (lane < U) ? Gw[lane * UP + j] : make_float2(0.f, 0.f);
-    if (j == lane) row[j].x += d.kappa;
-  }
-  int st = fin ? ST_OK : ST_NONFINITE;
-  if (st == ST_OK && !warp_gj_inverse<UP>(row, lane, U)) st = ST_NOT_PD;
   float sc = 0.f;
-  if (st == ST_OK) {
-    // t = sum_ij (T G)_ij conj(T_ij): lane i forms row i of T G
-    float part = 0.f;
-#pragma unroll
-    for (int j = 0; j < UP; ++j) {
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < UP; ++k) cmac(acc, row[k], Gw[k * UP + j]);
-      part = fmaf(acc.x, row[j].x, fmaf(acc.y, row[j].y, part));
-    }
-    if (lane >= U) part = 0.f;
-    const float t = warp_sum(part);
-    if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-    else sc = sqrtf(d.rho2_sys / (d.Es * t));
-  }
-  float2 *zdst = Z + (size_t)sys * K * U;
-  for (int k = 0; k < K; ++k) {
-    float2 acc = make_float2(0.f, 0.f);
-    if (st == ST_OK) {
-#pragma unroll
-      for (int j = 0; j < UP; ++j) cmac(acc, row[j], Sw[k * UP + j]);
-    }
-    if (lane < U) zdst[(size_t)k * U + lane] = acc;
-  }
+  const int st = warp_solve<UP>(Gw, Sw, Z + (size_t)sys * K * U, U, d.kappa, d.rho2_sys, d.Es, U,
+                                K, lane, fin, sc);
   if (lane == 0) {
     scale[sys] = sc;
     report(status, sys, st);

@@ -28,4 +28,9 @@ cudaError_t launch_apply(const SysDesc &d, int UP, const float2 *H, const float2
 cudaError_t launch_fused(const SysDesc &d, int UP, int maxrows, const float2 *H, const float2 *S,
                          float2 *X, int *status, float *scale_out, cudaStream_t s);
 
+// Reduced-precision fused path (tensor-core Gram): users padded to <= 32.
+bool tc_supported(int UP);
+cudaError_t launch_fused_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
+                            float2 *X, int *status, float *scale_out, cudaStream_t s);
+
 }  // namespace dp

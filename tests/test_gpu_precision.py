@@ -1,0 +1,109 @@
+"""Reduced-precision form: Gram on the tensor cores (BF16 / FP16 inputs, FP32
+accumulation), solve and apply in FP32; against the FP64 oracle at the 1e-3
+relative-error bar, i.i.d. and Kronecker-correlated channels."""
+import numpy as np
+import pytest
+
+from gpu_util import gpu_precode, oracle_of, rel_err_per_sc, to_dev
+from paper_1804_10987_gb300 import dp, synth
+
+pytestmark = pytest.mark.gpu
+TOL_LP = 1e-3
+
+
+def check(p, prec, mode=None, tau=None, tol=TOL_LP):
+    Xg, st = gpu_precode(p, mode, tau, prec=prec)
+    ref = oracle_of(p, mode, tau)
+    assert np.array_equal(st, ref["status"])
+    err = rel_err_per_sc(Xg, ref["X"])
+    assert err.max() <= tol, f"{prec}: max rel err {err.max():.3e} median {np.median(err):.3e}"
+    return err
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("channel", ["iid", "kron"])
+def test_c3_shape_sampled(prec, channel):
+    """U = 32, B = 512, C = 16 clusters of 32, 64-QAM, 10 dB (a 200-subcarrier
+    draw; the full 3300-subcarrier slot is checked on samples below)."""
+    p = synth.make_problem(32, 512, 16, 200, 14, 64, 10.0, seed=synth.seed_for(3, 1),
+                           channel=channel)
+    check(p, prec)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("channel", ["iid", "kron"])
+def test_c3_full_size_sampled_outputs(prec, channel):
+    """The full slot (3300 subcarriers) in the benchmark's launch configuration;
+    the oracle recomputes 96 sampled subcarriers one by one."""
+    import torch
+    import oracle
+    U, B, C, n_sc, K = 32, 512, 16, 3300, 14
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.seed_for(3, 7))
+    H = synth.torch_channel(n_sc, B, U, channel, gen, "cuda")
+    S = synth.torch_symbols(64, (n_sc, K, U), gen, "cuda")
+    N0 = synth.n0_from_snr(10.0)
+    pl = dp.Plan(U, B, C, n_sc, K, mode="wf", prec=prec, N0=N0)
+    X = pl.empty("X")
+    pl.precode(H, S, X)
+    assert (pl.status_get() == 0).all()
+    idx = np.sort(np.random.default_rng(3).choice(n_sc, 96, replace=False))
+    ref = oracle.precode(H[idx].cpu().numpy(), S[idx].cpu().numpy(), [32] * C, "wf", N0=N0,
+                         nthreads=8)
+    err = rel_err_per_sc(X[idx].cpu().numpy(), ref["X"])
+    assert err.max() <= TOL_LP, err.max()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("mode,tau", [("wf", 0.125), ("zf", 0.125), ("fdwf", 0.125),
+                                      ("fdwf", 1.0)])
+def test_c2_shape_modes(prec, mode, tau):
+    p = synth.make_problem(16, 256, 8, 300, 14, 16, 10.0, seed=synth.seed_for(2, 50),
+                           mode=mode, tau=tau)
+    check(p, prec, mode, tau)
+
+
+@pytest.mark.parametrize("U,cs,n_sc,K,mode", [
+    (8, [32, 32], 37, 14, "wf"),          # 8 systems per CTA, ragged last group
+    (24, [100, 60], 5, 3, "wf"),          # 48 realified rows per system, pad rows
+    (12, [200], 9, 5, "fdwf"),            # U pads to 16, one cluster
+    (6, [3, 90, 40], 4, 2, "fdwf"),       # B_c < U cluster, ragged chunks
+    (32, [1000], 3, 14, "wf"),            # 16 chunks of 64 antennas
+    (5, [20, 20], 6, 4, "wf"),            # odd U: plain-load staging
+])
+def test_tc_shapes(U, cs, n_sc, K, mode):
+    p = synth.make_problem(U, sum(cs), len(cs), n_sc, K, 16, 12.0, seed=2000 + U + n_sc,
+                           mode=mode, cluster_sizes=cs)
+    for prec in ("bf16", "fp16"):
+        check(p, prec)
+
+
+def test_tc_nonfinite_isolated():
+    p = synth.make_problem(16, 256, 8, 12, 14, 16, 10.0, seed=31)
+    p.H[3, 100, 4] = np.nan
+    p.S[7, 2, 1] = np.nan
+    Xg, st = gpu_precode(p, prec="bf16")
+    assert st[3] == dp.NONFINITE and st[7] == dp.NONFINITE
+    assert np.all(Xg[3] == 0) and np.all(Xg[7] == 0)
+    ok = np.setdiff1d(np.arange(12), [3, 7])
+    ref = oracle_of(p)
+    assert rel_err_per_sc(Xg[ok], ref["X"][ok]).max() < TOL_LP
+
+
+def test_tc_deterministic_and_batch_independent():
+    p = synth.make_problem(16, 256, 8, 40, 14, 16, 10.0, seed=32)
+    a, _ = gpu_precode(p, prec="fp16")
+    b, _ = gpu_precode(p, prec="fp16")
+    assert np.array_equal(a, b)
+    sub = synth.Problem(p.U, p.B, p.cluster_sizes, 8, p.K, p.H[12:20].copy(), p.S[12:20].copy(),
+                        p.rho2, p.N0, p.Es, p.tau, p.mode)
+    c, _ = gpu_precode(sub, prec="fp16")
+    assert np.array_equal(a[12:20], c)
+
+
+def test_fp16_more_accurate_than_bf16():
+    p = synth.make_problem(32, 512, 16, 64, 14, 64, 20.0, seed=33, channel="kron")
+    eb = check(p, "bf16")
+    ef = check(p, "fp16")
+    assert np.median(ef) < np.median(eb)
+    _ = to_dev
