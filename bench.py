@@ -31,9 +31,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="c2", U=16, B=256, C=8, n_sc=1200, K=14, qam=16, snr_db=10.0)
-KERNEL_SOURCES = ["paper_1804_10987_gb300/csrc/dp_fp32.cu",
-                  "paper_1804_10987_gb300/csrc/dp_blocks.cuh",
-                  "paper_1804_10987_gb300/csrc/dp_common.cuh"]
+KERNEL_SOURCES = {
+    "fp32": ["paper_1804_10987_gb300/csrc/dp_fp32.cu", "paper_1804_10987_gb300/csrc/dp_blocks.cuh",
+             "paper_1804_10987_gb300/csrc/dp_common.cuh"],
+    "tc": ["paper_1804_10987_gb300/csrc/dp_tc.cu", "paper_1804_10987_gb300/csrc/dp_tc.cuh",
+           "paper_1804_10987_gb300/csrc/dp_blocks.cuh", "paper_1804_10987_gb300/csrc/dp_common.cuh"],
+}
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -44,6 +47,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["wf", "zf", "fdwf"], default="wf")
+    ap.add_argument("--prec", choices=["fp32", "bf16", "fp16"], default="fp16",
+                    help="Gram arithmetic of the headline path")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip timing the plain FP32 path beside the headline path")
     ap.add_argument("--slots", type=int, default=8, help="slots of 1200 subcarriers per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -60,14 +67,18 @@ def dist_env():
 
 
 def metric_name(mode):
-    return f"precoded subcarriers/s ({mode.upper()}, U=16 B=256 C=8 K=14, complex64)"
+    return f"precoded subcarriers/s ({mode.upper()}, U=16 B=256 C=8 K=14, complex64 I/O)"
+
+
+def kernel_name(prec):
+    return "k_fused<16>" if prec == "fp32" else f"k_fused_tc<16,{'bf16' if prec == 'bf16' else 'fp16'}>"
 
 
 def config_dict(args, world, slots):
     w = WORKLOAD
     return {"workload": f"c2: U={w['U']} B={w['B']} C={w['C']}x32 n_sc={w['n_sc']}/slot "
                         f"K={w['K']} {w['qam']}-QAM SNR {w['snr_db']:g} dB iid Rayleigh",
-            "mode": args.mode, "slots_per_step": slots,
+            "mode": args.mode, "prec": args.prec, "slots_per_step": slots,
             "subcarriers_per_step": w["n_sc"] * slots,
             "l2": "inputs larger than L2 (331 MB per step of 8 slots vs 129 MB L2)",
             "parallelism": f"replicas x{world}"}
@@ -143,20 +154,28 @@ def make_slot_host(slot_index: int, mode: str):
                               seed=synth.seed_for(2, 100 + slot_index), mode=mode)
 
 
-def cpu_oracle_rate(mode: str, seconds: float, steps=None):
+def rel_err_max(Xg, Xr):
+    import numpy as np
+    n = Xr.shape[0]
+    d = np.linalg.norm((Xg.astype(np.complex128) - Xr).reshape(n, -1), axis=1)
+    r = np.linalg.norm(Xr.reshape(n, -1), axis=1)
+    return float((d / np.where(r > 0, r, 1.0)).max())
+
+
+def cpu_oracle_rate(mode: str, seconds: float, steps=None, problem=None):
     """Time the FP64 oracle, as it stands, on the host cores: slots of 1200
     subcarriers until `seconds` elapse (or `steps` slots).  Returns
-    (subcarriers/s, cores, sample description, per-step seconds)."""
+    (subcarriers/s, cores, sample description, per-step seconds, X of the slot)."""
     import oracle
-    p = make_slot_host(0, mode)
+    p = problem if problem is not None else make_slot_host(0, mode)
     cores = os.cpu_count() or 1
     oracle.build()
     per = []
     t_end = time.perf_counter() + seconds
     while True:
         t0 = time.perf_counter()
-        oracle.precode(p.H, p.S, p.cluster_sizes, mode, rho2=p.rho2, N0=p.N0, Es=p.Es,
-                       tau=p.tau, nthreads=cores, outputs=("X",))
+        out = oracle.precode(p.H, p.S, p.cluster_sizes, mode, rho2=p.rho2, N0=p.N0, Es=p.Es,
+                             tau=p.tau, nthreads=cores, outputs=("X",))
         per.append(time.perf_counter() - t0)
         if steps is not None and len(per) >= steps:
             break
@@ -165,21 +184,21 @@ def cpu_oracle_rate(mode: str, seconds: float, steps=None):
     rate = p.n_sc * len(per) / sum(per)
     sample = (f"{len(per)} x one slot of {p.n_sc} subcarriers (U=16, B=256, K=14, {mode}), "
               f"{cores} threads")
-    return rate, cores, sample, per
+    return rate, cores, sample, per, out["X"]
 
 
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    _, cores, _, _ = cpu_oracle_rate(args.mode, 0.0, steps=max(1, args.warmup))
-    rate, cores, sample, per = cpu_oracle_rate(args.mode, 0.0, steps=max(1, args.steps))
+    cpu_oracle_rate(args.mode, 0.0, steps=max(1, args.warmup))
+    rate, cores, sample, per, _ = cpu_oracle_rate(args.mode, 0.0, steps=max(1, args.steps))
     ms = 1e3 * sum(per) / len(per)
     line = {"impl": "reference", "metric": metric_name(args.mode), "value": rate,
             "unit": "subcarriers/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(config_dict(args, 1, 1), slots_per_step=1,
+            "config": dict(config_dict(args, 1, 1), slots_per_step=1, prec="f64 oracle",
                            subcarriers_per_step=WORKLOAD["n_sc"]),
             "cpu_baseline": {"value": rate, "unit": "subcarriers/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
@@ -189,23 +208,24 @@ def reference_arm(args):
 
 
 # ----------------------------------------------------------- our arm ---------
-def sources_hash():
+def sources_hash(kind):
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES[kind]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(subcarriers_per_launch):
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, scaled by subcarriers; None if missing or taken on other code."""
+def traffic_per_launch(kernel, subcarriers_per_launch):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, scaled
+    by subcarriers; None if missing or taken on other code."""
     try:
         with open(TRAFFIC_FILE) as f:
-            t = json.load(f)
+            t = json.load(f)[kernel]
     except Exception:
         return None
-    if t.get("sources_hash") != sources_hash():
+    kind = "fp32" if kernel.startswith("k_fused<") else "tc"
+    if t.get("sources_hash") != sources_hash(kind):
         return None
     return t["dram_bytes_per_subcarrier"] * subcarriers_per_launch
 
@@ -242,57 +262,75 @@ def our_arm(args):
     H = synth.torch_channel(n_sc, B, U, "iid", gen, "cuda")
     S = synth.torch_symbols(w["qam"], (n_sc, K, U), gen, "cuda")
     X = torch.empty((n_sc, K, B), dtype=torch.complex64, device="cuda")
-    plan = dp.Plan(U, B, C, n_sc, K, mode=args.mode, N0=N0, tau=0.125, stream=stream)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        plan.precode(H, S, X)
-    st = plan.status_get()
-    assert (st == 0).all(), "precoding reported failures"
+    def time_path(prec, Xout, sample_clocks):
+        plan = dp.Plan(U, B, C, n_sc, K, mode=args.mode, prec=prec, N0=N0, tau=0.125,
+                       stream=stream)
+        for _ in range(args.warmup):
+            plan.precode(H, S, Xout)
+        st = plan.status_get()
+        assert (st == 0).all(), f"{prec}: precoding reported failures"
+        sampler = None
+        if sample_clocks:
+            bus = None
+            try:
+                bus = torch.cuda.get_device_properties(local).pci_bus_id
+            except Exception:
+                bus = None
+            sampler = ClockSampler(bus)
+            sampler.start()
+        torch.cuda.synchronize()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            plan.precode(H, S, Xout)
+            ev[i][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms_total = t0.elapsed_time(t1)
+        launch_ms = [a.elapsed_time(b) for a, b in ev]
+        if world > 1:
+            t = torch.tensor([ms_total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_total = float(t.item())
+        return plan, ms_total, launch_ms, clocks
 
-    bus = None
-    try:
-        bus = torch.cuda.get_device_properties(local).pci_bus_id
-    except Exception:
-        bus = None
-    sampler = ClockSampler(bus)
-    sampler.start()
-    torch.cuda.synchronize()
-    barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for i in range(args.steps):
-        ev[i][0].record(stream)
-        plan.precode(H, S, X)
-        ev[i][1].record(stream)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    ms_total = t0.elapsed_time(t1)
-    launch_ms = [a.elapsed_time(b) for a, b in ev]
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    # algorithmic bytes of one launch: H once + S + X
+    alg_bytes = n_sc * (B * U * 8 + K * U * 8 + K * B * 8)
+    peak, peak_src = load_peaks()
+
+    def roofline_of(prec, launch_ms):
+        kern_s = statistics.mean(launch_ms) / 1e3
+        achieved = alg_bytes / kern_s / 1e9
+        return {"bound": "hbm", "kernel": kernel_name(prec), "achieved": achieved, "peak": peak,
+                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_per_launch(kernel_name(prec), n_sc),
+                "algorithmic_bytes": alg_bytes, "launch_ms_mean": kern_s * 1e3}
+
+    plain = None
+    X_plain = None
+    if args.prec != "fp32" and not args.no_plain:
+        X_plain = torch.empty_like(X)
+        pplan, p_ms, p_launch, _ = time_path("fp32", X_plain, False)
+        pplan.close()
+        plain = {"value": n_sc * args.steps * world / (p_ms / 1e3), "unit": "subcarriers/s",
+                 "ms_per_step": p_ms / args.steps, "dtype": "f32",
+                 "roofline": roofline_of("fp32", p_launch)}
+    plan, ms_total, launch_ms, clocks = time_path(args.prec, X, True)
     ms_step = ms_total / args.steps
     value = n_sc * args.steps * world / (ms_total / 1e3)
-
-    # roofline of the fused kernel: algorithmic bytes = H once + S + X
-    alg_bytes = n_sc * (B * U * 8 + K * U * 8 + K * B * 8)
-    kern_s = statistics.mean(launch_ms) / 1e3
-    peak, peak_src = load_peaks()
-    achieved = alg_bytes / kern_s / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_fused<16>", "achieved": achieved, "peak": peak,
-                "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_per_launch(n_sc), "algorithmic_bytes": alg_bytes,
-                "launch_ms_mean": kern_s * 1e3}
+    roofline = roofline_of(args.prec, launch_ms)
 
     # end to end through the public call with host buffers
     e2e = None
@@ -330,17 +368,31 @@ def our_arm(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample, _ = cpu_oracle_rate(args.mode, args.cpu_seconds)
+        # the oracle on the first slot of the timed input; its outputs also give
+        # the relative error of the timed GPU outputs on that slot
+        Hs = H[: w["n_sc"]].cpu().numpy()
+        Ss = S[: w["n_sc"]].cpu().numpy()
+        slot = synth.Problem(U, B, [B // C] * C, w["n_sc"], K, Hs, Ss, 1.0, N0, 1.0, 0.125,
+                             args.mode)
+        rate, cores, sample, _, Xref = cpu_oracle_rate(args.mode, args.cpu_seconds, problem=slot)
         cpu = {"value": rate, "unit": "subcarriers/s", "cores": cores, "kind": "oracle",
-               "sample": sample}
+               "sample": sample,
+               "rel_err_max": rel_err_max(X[: w["n_sc"]].cpu().numpy(), Xref)}
+        if X_plain is not None:
+            cpu["rel_err_max_plain_fp32"] = rel_err_max(X_plain[: w["n_sc"]].cpu().numpy(), Xref)
 
     plan.close()
     if rank == 0:
         line = {"metric": metric_name(args.mode), "value": value, "unit": "subcarriers/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32 (complex64)", "data": "synthetic",
+                "vs_baseline": None,
+                "dtype": "f32" if args.prec == "fp32" else f"{args.prec} Gram (tensor cores, f32 "
+                                                          "accumulate) + f32 solve/apply",
+                "data": "synthetic",
                 "config": config_dict(args, world, slots), "roofline": roofline,
+                "plain_fp32": plain,
+                "speedup_vs_plain_fp32": (value / plain["value"]) if plain else None,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
                 "clocks": clocks,
                 "vectors_per_s": value * K,

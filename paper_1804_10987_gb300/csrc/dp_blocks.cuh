@@ -13,6 +13,11 @@ namespace dp {
 
 constexpr int NT = 256;  // threads per CTA of the per-system kernels
 
+// Lemma 1 is used for t while kappa ||T||_F^2 <= kLemmaMaxRatio tr(T), i.e.
+// while its subtraction amplifies rounding errors by at most 1 / (1 - 0.875)
+// = 8; beyond that t is formed as tr(T G T).
+constexpr float kLemmaMaxRatio = 0.875f;
+
 constexpr int pow2_floor(int x) {
   int p = 1;
   while (p * 2 <= x) p *= 2;
@@ -191,11 +196,24 @@ __device__ int cta_gj_inverse(float2 *A, int U, int tid) {
   return ST_OK;
 }
 
-// t = tr(T G T) = sum_ij (T G)_ij conj(T_ij) with T = A^{-1}: the definition
-// tr(Q^H Q) of Thm. 1 through Eq. (14), free of the cancellation of the
-// Lemma 1 difference tr(T) - kappa ||T||_F^2 when kappa dominates G.
+// t = tr(Q^H Q) of Thm. 1 for T = A^{-1}: Lemma 1, tr(T) - kappa ||T||_F^2,
+// unless its subtraction cancels (kappa ||T||_F^2 > kLemmaMaxRatio tr(T));
+// then the definition through Eq. (14), tr(T G T) = sum_ij (T G)_ij conj(T_ij).
 template <int UP>
-__device__ float cta_trace_tgt(const float2 *T, const float2 *G, int U, float *red, int tid) {
+__device__ float cta_trace_tgt(const float2 *T, const float2 *G, float kappa, int U, float *red,
+                               int tid) {
+  float dg = 0.f, fr = 0.f;
+  for (int e = tid; e < U * UP; e += NT) {
+    const int i = e / UP, j = e - i * UP;
+    if (j < U) {
+      const float2 t = T[i * UP + j];
+      fr = fmaf(t.x, t.x, fmaf(t.y, t.y, fr));
+      if (i == j) dg += t.x;
+    }
+  }
+  const float tr = cta_sum(dg, red, tid);
+  const float fro = cta_sum(fr, red, tid);
+  if (kappa * fro <= kLemmaMaxRatio * tr) return tr - kappa * fro;
   float part = 0.f;
   for (int e = tid; e < U * UP; e += NT) {
     const int i = e / UP, j = e - i * UP;
@@ -223,36 +241,82 @@ __device__ void cta_whiten(const float2 *T, const float2 *Ss, float2 *Zs, int U,
 }
 
 // ----------------------------------------------------------------- apply ---
+// acc[r][q] += sum_u conj(h_r[u]) z_q[u] for R antenna rows and NQ symbols:
+// h rows in shared memory (UP complex, 16-byte aligned), z_q = zs + q * UP.
+// Fully unrolled with compile-time R, NQ: every broadcast z load feeds R
+// complex multiply-adds and no predicate sits in the inner loop.
+template <int UP, int R, int NQ>
+__device__ __forceinline__ void apply_tile(const float *const (&hrow)[R], const float2 *zs,
+                                           float2 (&acc)[R][NQ]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[r][q] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int u = 0; u < UP; u += 2) {
+    float4 g[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) g[r] = *reinterpret_cast<const float4 *>(hrow[r] + 2 * u);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const float4 z = *reinterpret_cast<const float4 *>(zs + q * UP + u);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        cmac_cj(acc[r][q], make_float2(g[r].x, g[r].y), make_float2(z.x, z.y));
+        cmac_cj(acc[r][q], make_float2(g[r].z, g[r].w), make_float2(z.z, z.w));
+      }
+    }
+  }
+}
+
+// X[k][b_r] = scale * sum_u conj(H[b_r][u]) z_k[u] for k in [k0, k1), rows
+// r < R (row r stored only if r < nvalid), symbols in blocks of up to 7.
+template <int UP, int R>
+__device__ __forceinline__ void apply_rows_k(const float *const (&hrow)[R], int nvalid,
+                                             const float2 *zs, int k0, int k1, float scale,
+                                             float2 *const (&xcol)[R], int ldx) {
+  for (int kb = k0; kb < k1; kb += 7) {
+    const int nq = min(7, k1 - kb);
+    const float2 *z = zs + kb * UP;
+#define DP_APPLY_CASE(NQ)                                                \
+  case NQ: {                                                             \
+    float2 acc[R][NQ];                                                   \
+    apply_tile<UP, R, NQ>(hrow, z, acc);                                 \
+    _Pragma("unroll") for (int r = 0; r < R; ++r) {                      \
+      if (r < nvalid) {                                                  \
+        _Pragma("unroll") for (int q = 0; q < NQ; ++q)                   \
+            xcol[r][(size_t)(kb + q) * ldx] = cscale(acc[r][q], scale);  \
+      }                                                                  \
+    }                                                                    \
+    break;                                                               \
+  }
+    switch (nq) {
+      DP_APPLY_CASE(7)
+      DP_APPLY_CASE(6)
+      DP_APPLY_CASE(5)
+      DP_APPLY_CASE(4)
+      DP_APPLY_CASE(3)
+      DP_APPLY_CASE(2)
+      DP_APPLY_CASE(1)
+      default: break;
+    }
+#undef DP_APPLY_CASE
+  }
+}
+
 // X[k][lo + r] = scale * sum_u conj(H[r][u]) z[k][u] for the tile rows r <
-// nrows; z from shared Zs [K][UP] (pad entries zero).  Thread per row, rows
-// tid + j NT; K in blocks of KB accumulators.  Stores are coalesced along b.
+// nrows; z from shared Zs [K][UP] (pad entries zero).  Thread per row pair
+// (r, r + NT), all symbols; stores are coalesced along b.
 template <int UP, int KB>
 __device__ void apply_rows(const float *Hs, int nrows, const float2 *Zs, int K, float scale,
                            float2 *__restrict__ Xn, int B, int lo, int tid) {
   constexpr int RS = Geo<UP>::RS;
-  for (int r = tid; r < nrows; r += NT) {
-    const float *hrow = Hs + r * RS;
-    for (int kb = 0; kb < K; kb += KB) {
-      float2 acc[KB];
-#pragma unroll
-      for (int kk = 0; kk < KB; ++kk) acc[kk] = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int u = 0; u < UP; u += 2) {
-        const float4 h = *reinterpret_cast<const float4 *>(hrow + 2 * u);
-        const float2 h0 = make_float2(h.x, h.y), h1 = make_float2(h.z, h.w);
-#pragma unroll
-        for (int kk = 0; kk < KB; ++kk) {
-          if (kb + kk < K) {
-            const float4 z = *reinterpret_cast<const float4 *>(Zs + (kb + kk) * UP + u);
-            cmac_cj(acc[kk], h0, make_float2(z.x, z.y));
-            cmac_cj(acc[kk], h1, make_float2(z.z, z.w));
-          }
-        }
-      }
-#pragma unroll
-      for (int kk = 0; kk < KB; ++kk)
-        if (kb + kk < K) Xn[(size_t)(kb + kk) * B + lo + r] = cscale(acc[kk], scale);
-    }
+  static_assert(KB == 7, "blocks of seven symbols");
+  for (int r = tid; r < nrows; r += 2 * NT) {
+    const int r1 = r + NT < nrows ? r + NT : r;
+    const float *hrow[2] = {Hs + r * RS, Hs + r1 * RS};
+    float2 *xcol[2] = {Xn + lo + r, Xn + lo + r1};
+    apply_rows_k<UP, 2>(hrow, r + NT < nrows ? 2 : 1, Zs, 0, K, scale, xcol, B);
   }
 }
 
@@ -330,17 +394,33 @@ __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int 
   if (st == ST_OK && !warp_gj_inverse<UP>(row, lane, U)) st = ST_NOT_PD;
   float sc = 0.f;
   if (st == ST_OK) {
-    // t = sum_ij (T G)_ij conj(T_ij): lane i forms row i of T G
-    float part = 0.f;
+    // Lemma 1: t = tr(T) - kappa ||T||_F^2.  When kappa ||T||_F^2 / tr(T) is
+    // close to one the difference cancels (kappa dominating G); then t is
+    // formed as the definition tr(T G T) = sum_ij (T G)_ij conj(T_ij).
+    float dg = 0.f, fr = 0.f;
 #pragma unroll
     for (int j = 0; j < UP; ++j) {
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < UP; ++k) cmac(acc, row[k], Gs[k * UP + j]);
-      part = fmaf(acc.x, row[j].x, fmaf(acc.y, row[j].y, part));
+      if (j == lane) dg = row[j].x;
+      fr = fmaf(row[j].x, row[j].x, fmaf(row[j].y, row[j].y, fr));
     }
-    if (lane >= U) part = 0.f;
-    const float t = warp_sum(part);
+    if (lane >= U) {
+      dg = 0.f;
+      fr = 0.f;
+    }
+    const float tr = warp_sum(dg), fro = warp_sum(fr);
+    float t = tr - kappa * fro;
+    if (kappa * fro > kLemmaMaxRatio * tr) {
+      float part = 0.f;
+#pragma unroll
+      for (int j = 0; j < UP; ++j) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < UP; ++k) cmac(acc, row[k], Gs[k * UP + j]);
+        part = fmaf(acc.x, row[j].x, fmaf(acc.y, row[j].y, part));
+      }
+      if (lane >= U) part = 0.f;
+      t = warp_sum(part);
+    }
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
     else sc = sqrtf(rho2 / (Es * t));
   }

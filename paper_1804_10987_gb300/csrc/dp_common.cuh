@@ -17,9 +17,11 @@ enum : int {
 };
 
 constexpr unsigned FULL = 0xffffffffu;
-// Iteration bound of every spin on an mbarrier: each try_wait suspends for a
-// bounded hardware interval, so this caps a wait at well under a second.
+// Iteration bound of every spin on an mbarrier.  After a few immediate
+// retries each iteration also sleeps ~64 ns, so a wait gives up after well
+// under a second instead of hanging.
 constexpr uint32_t kWaitIters = 1u << 22;
+constexpr uint32_t kSpinBeforeSleep = 8;
 
 // ---------------------------------------------------------------- complex ---
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -104,9 +106,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 // Bounded wait for the phase with the given parity to complete.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kWaitIters; ++i)
+  for (uint32_t i = 0; i < kWaitIters; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (i >= kSpinBeforeSleep) __nanosleep(64);
+  }
   return false;
+}
+
+// CTA-wide wait: one thread polls the barrier, the others park at the CTA
+// barrier (no issue slots spent spinning).  Returns false on timeout, the
+// same value in every thread.
+__device__ __forceinline__ bool mbar_wait_cta(uint64_t *bar, uint32_t parity) {
+  bool ok = true;
+  if (threadIdx.x == 0) ok = mbar_wait(bar, parity);
+  return __syncthreads_and(ok) != 0;
 }
 
 // ---------------------------------------------------------- parameters ----

@@ -61,10 +61,13 @@ __global__ void __launch_bounds__(NT) k_gram(SysDesc d, const float2 *__restrict
     }
     fetch_rows<UP>(Hs, Hn, lo + c0, m, d.U, tma, bar, tid);
     if (tma) {
-      if (!mbar_wait(bar, it & 1)) timeout = true;
+      if (!mbar_wait_cta(bar, it & 1)) timeout = true;
+    } else {
+      __syncthreads();
     }
-    if (__syncthreads_or(timeout)) {
-      if (tma) mbar_wait(bar, it & 1);  // let copies in flight land before exiting
+    if (timeout) {
+      if (tid == 0) mbar_wait(bar, it & 1);  // let copies in flight land before exiting
+      __syncthreads();
       break;
     }
     ga.accumulate(Hs, m);
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(NT) k_solve_cta(SysDesc d, const float2 *__res
   float sc = 0.f;
   if (st == ST_OK) st = cta_gj_inverse<UP>(A, U, tid);
   if (st == ST_OK) {
-    const float t = cta_trace_tgt<UP>(A, G, U, red, tid);
+    const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
     else sc = sqrtf(d.rho2_sys / (d.Es * t));
   }
@@ -244,10 +247,13 @@ __global__ void __launch_bounds__(NT) k_apply(SysDesc d, const float2 *__restric
     }
     fetch_rows<UP>(Hs, Hn, lo + c0, m, U, tma, bar, tid);
     if (tma) {
-      if (!mbar_wait(bar, it & 1)) timeout = true;
+      if (!mbar_wait_cta(bar, it & 1)) timeout = true;
+    } else {
+      __syncthreads();
     }
-    if (__syncthreads_or(timeout)) {
-      if (tma) mbar_wait(bar, it & 1);
+    if (timeout) {
+      if (tid == 0) mbar_wait(bar, it & 1);
+      __syncthreads();
       zero_rows<UP>(nrows, K, Xn, d.B, lo, tid);
       return;
     }
@@ -291,9 +297,10 @@ __global__ void __launch_bounds__(NT) k_fused(SysDesc d, const float2 *__restric
   fetch_rows<UP>(Hs, H + (size_t)n * d.B * U, lo, nrows, U, tma, bar, tid);
   const bool sfin = load_symbols<UP>(S + (size_t)n * K * U, Ss, U, K, tid);
   bool timeout = false;
-  if (tma) timeout = !mbar_wait(bar, 0);
-  if (__syncthreads_or(timeout)) {
-    if (tma) mbar_wait(bar, 0);
+  if (tma) timeout = !mbar_wait_cta(bar, 0);
+  if (timeout) {
+    if (tid == 0) mbar_wait(bar, 0);
+    __syncthreads();
     zero_rows<UP>(nrows, K, Xn, d.B, lo, tid);
     if (tid == 0) {
       report(status, sys, ST_TIMEOUT);
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(NT) k_fused(SysDesc d, const float2 *__restric
   float sc = 0.f;
   if (st == ST_OK) st = cta_gj_inverse<UP>(A, U, tid);
   if (st == ST_OK) {
-    const float t = cta_trace_tgt<UP>(A, G, U, red, tid);
+    const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
     else sc = sqrtf(d.rho2_sys / (d.Es * t));
   }

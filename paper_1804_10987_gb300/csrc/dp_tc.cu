@@ -8,13 +8,15 @@
 // G = H H^H).  The group's realified rows are stacked into the M = 128 rows
 // of one K-major operand that serves as both A and B (D = R R^T, N = 128);
 // the block-diagonal blocks of D are the systems' P.  Antennas stream in
-// chunks of 64: one bulk copy per system and chunk into an FP32 staging
-// buffer, conversion to BF16/FP16 into a 128-byte-swizzled tile (two tiles
-// alternate so conversion of chunk c+1 overlaps the MMAs of chunk c), four
+// chunks of 64: coalesced 8-byte loads of H straight into registers,
+// conversion to BF16/FP16 into a 128-byte-swizzled tile (two tiles alternate
+// so that the conversion of chunk c+1 overlaps the MMAs of chunk c), four
 // MMAs of K = 16 per chunk accumulating in TMEM.
 // Then: TMEM -> shared P -> G, warp-per-system Gauss-Jordan solve in
 // registers (Thm. 1, Lemma 1 through tr(T G T), z = A^{-1} s), and the FP32
-// apply x_c = scale H_c^H z over the antenna rows fetched again (from L2).
+// apply x_c = scale H_c^H z over antenna rows bulk-copied again (from L2)
+// into padded shared rows.  The 32 KB tile region is reused for P and for
+// the apply rows, which keeps three to four CTAs on an SM.
 #include "dp_blocks.cuh"
 #include "dp_internal.h"
 #include "dp_tc.cuh"
@@ -22,7 +24,8 @@
 namespace dp {
 namespace {
 
-constexpr int KC = 64;          // antennas per chunk (one 128-byte K-block of 16-bit data)
+constexpr int KC = 64;          // antennas per Gram chunk (one 128-byte K-block of 16-bit data)
+constexpr int KA = 64;          // antenna rows per system and apply chunk
 constexpr int TILE_BYTES = 128 * 128;
 constexpr int TMEM_COLS = 128;
 
@@ -30,15 +33,24 @@ template <int UP>
 struct TcGeo {
   static constexpr int NG = (128 / (2 * UP)) > 0 ? 128 / (2 * UP) : 1;  // systems per CTA
   static constexpr int RS = Geo<UP>::RS;
-  static constexpr int PS = 2 * UP + 1;                          // row stride of a P block
-  static constexpr int STAGE_FLOATS = NG * KC * RS;              // padded rows (apply)
-  static constexpr int P_FLOATS = NG * 2 * UP * PS;
-  static_assert(P_FLOATS <= STAGE_FLOATS, "P aliases the staging buffer");
-  static_assert(NG * KC * 2 * UP <= STAGE_FLOATS, "unpadded Gram staging fits");
+  static constexpr int M2 = 2 * UP;
+  // one region holds the two tiles, then P, then the apply rows
+  static constexpr int APPLY_BYTES = NG * KA * RS * 4;
+  static constexpr int REGION = APPLY_BYTES > 2 * TILE_BYTES ? APPLY_BYTES : 2 * TILE_BYTES;
+  // P blocks padded by one float, or XOR-swizzled when that does not fit
+  static constexpr bool P_PAD = (size_t)NG * M2 * (M2 + 1) * 4 <= REGION;
+  static constexpr int PS = P_PAD ? M2 + 1 : M2;
+  static_assert(P_PAD || (M2 % 32 == 0), "swizzled P needs 32-float rows");
+  static_assert((size_t)NG * M2 * PS * 4 <= REGION, "P fits the region");
+  static_assert((size_t)NG * KA * RS * 4 <= REGION, "apply rows fit the region");
+  static constexpr int MIN_BLOCKS = UP <= 16 ? 2 : 1;
+  __device__ static __forceinline__ int p_index(int s, int r, int c) {
+    return (s * M2 + r) * PS + (P_PAD ? c : (c ^ (r & 31)));
+  }
 };
 
 struct TcSmem {
-  size_t tiles, stage, G, S, Z, scale, status, info, bars, tmem, total;
+  size_t region, G, S, Z, scale, status, info, bars, tmem, total;
 };
 
 template <int UP>
@@ -52,8 +64,7 @@ __host__ __device__ TcSmem tc_smem_layout(int K) {
     o += bytes;
     return at;
   };
-  L.tiles = take(2 * TILE_BYTES, 1024);
-  L.stage = take((size_t)T::STAGE_FLOATS * 4, 128);
+  L.region = take(T::REGION, 1024);
   L.G = take((size_t)T::NG * UP * UP * 8, 16);
   L.S = take((size_t)T::NG * K * UP * 8 + 16, 16);
   L.Z = take((size_t)T::NG * K * UP * 8 + 16, 16);
@@ -67,20 +78,18 @@ __host__ __device__ TcSmem tc_smem_layout(int K) {
 }
 
 template <int UP, bool BF16>
-__global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__restrict__ H,
-                                                 const float2 *__restrict__ S,
-                                                 float2 *__restrict__ X,
-                                                 int *__restrict__ status,
-                                                 float *__restrict__ scale_out) {
+__global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
+    k_fused_tc(SysDesc d, const float2 *__restrict__ H, const float2 *__restrict__ S,
+               float2 *__restrict__ X, int *__restrict__ status, float *__restrict__ scale_out) {
   using T = TcGeo<UP>;
-  constexpr int NG = T::NG, RS = T::RS, PS = T::PS;
+  constexpr int NG = T::NG, RS = T::RS, M2 = T::M2;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const TcSmem L = tc_smem_layout<UP>(d.K);
-  unsigned char *tiles = base + L.tiles;
-  float *stage = reinterpret_cast<float *>(base + L.stage);
-  float *P = stage;  // alias: P is written after the last staged chunk was consumed
+  unsigned char *tiles = base + L.region;
+  float *P = reinterpret_cast<float *>(base + L.region);
+  float *stage = reinterpret_cast<float *>(base + L.region);
   float2 *Gs = reinterpret_cast<float2 *>(base + L.G);
   float2 *Ss = reinterpret_cast<float2 *>(base + L.S);
   float2 *Zs = reinterpret_cast<float2 *>(base + L.Z);
@@ -100,7 +109,7 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
   const int nact = min(NG, total - sys0);
   const bool tma = d.tma_ok != 0;
 
-  // rows of each system of the group
+  // ---- set-up: systems of the group, barriers, TMEM, symbols ---------------
   if (tid < NG) {
     int lo = 0, hi = 0, n = 0;
     if (tid < nact) {
@@ -112,12 +121,6 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
     nr_s[tid] = hi - lo;
     n_s[tid] = n;
   }
-  __syncthreads();
-  int kmax = 0;
-  for (int s = 0; s < NG; ++s) kmax = max(kmax, nr_s[s]);
-  const int nchunks = (kmax + KC - 1) / KC;
-
-  // ---- set-up: barriers, TMEM, symbols -----------------------------------
   if (tid == 0) {
     mbar_init(bar_tma, 1);
     mbar_init(bar_mma, 1);
@@ -128,85 +131,62 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
     tc::tmem_alloc(tmem_holder, TMEM_COLS);
     tc::tmem_relinquish();
   }
+  // rows of the tiles above the group's realified rows stay zero
+  if constexpr (NG * M2 < 128) {
+    constexpr int FREE = (128 - NG * M2) * 8;
+    for (int e = tid; e < 2 * FREE; e += NT) {
+      const int t = e / FREE, rem = e - t * FREE;
+      const int m = NG * M2 + rem / 8, g8 = rem % 8;
+      *reinterpret_cast<uint4 *>(tiles + t * TILE_BYTES + tc::sw128_offset(m, g8)) =
+          make_uint4(0, 0, 0, 0);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *tmem_holder;
+  int kmax = 0;
+  for (int s = 0; s < NG; ++s) kmax = max(kmax, nr_s[s]);
+  const int nchunks = (kmax + KC - 1) / KC;
   for (int e = tid; e < NG * K * UP; e += NT) {
     const int s = e / (K * UP), r = e - s * K * UP, k = r / UP, u = r - k * UP;
     float2 v = make_float2(0.f, 0.f);
     if (s < nact && u < U) v = __ldg(S + ((size_t)n_s[s] * K + k) * U + u);
     Ss[e] = v;
   }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t taddr = *tmem_holder;
 
-  // ---- Gram mainloop ----------------------------------------------------
+  // ---- Gram mainloop --------------------------------------------------------
   const uint32_t idesc = tc::idesc_f16(128, 128, BF16);
   const uint32_t tiles_u32 = smem_u32(tiles);
-  bool timeout = false;
-  for (int c = 0; c < nchunks; ++c) {
+  bool ok = true;
+  for (int c = 0; c < nchunks && ok; ++c) {
     const int buf = c & 1;
-    if (c > 0) {
-      __syncthreads();  // everyone finished reading the staging buffer
-      fence_proxy_async_smem();
-    }
-    // stage chunk c of every system (FP32, rows unpadded: row stride 2U floats)
-    if (tma) {
-      if (warp == 0) {
-        uint32_t bytes = 0;
-#pragma unroll
-        for (int s = 0; s < NG; ++s) {
-          const int m = min(KC, nr_s[s] - c * KC);
-          if (m > 0) bytes += (uint32_t)m * U * 8u;
-        }
-        if (lane == 0) {
-          if (bytes) mbar_arrive_expect_tx(bar_tma, bytes);
-          else mbar_arrive(bar_tma);
-        }
-        __syncwarp();
-        if (lane < NG) {
-          const int s = lane;
-          const int m = min(KC, nr_s[s] - c * KC);
-          if (m > 0)
-            tma_load_1d(stage + (size_t)s * KC * 2 * U,
-                        H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KC) * U, (uint32_t)m * U * 8u,
-                        bar_tma);
-        }
-      }
-      if (!mbar_wait(bar_tma, c & 1)) timeout = true;
-    } else {
-      for (int s = 0; s < NG; ++s) {
-        const int m = min(KC, nr_s[s] - c * KC);
-        const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KC) * U;
-        for (int e = tid; e < m * U; e += NT)
-          reinterpret_cast<float2 *>(stage + (size_t)s * KC * 2 * U)[e] = __ldg(src + e);
-      }
-    }
-    // the MMAs of chunk c - 2 read this tile: wait for them
-    if (c >= 2 && !mbar_wait(bar_mma + buf, ((c >> 1) - 1) & 1)) timeout = true;
-    if (__syncthreads_or(timeout)) break;
-
-    // convert: tile row m = s * 2UP + r (r < UP: Re H[.][r], else Im H[.][r - UP]),
-    // 8 consecutive antennas per 16-byte chunk, zero outside the systems
+    // the MMAs of chunk c - 2 read this tile
+    if (c >= 2) ok = mbar_wait_cta(bar_mma + buf, ((c >> 1) - 1) & 1);
+    if (!ok) break;
+    // item = (antenna octet g8, system s, user u): eight coalesced 8-byte
+    // loads, Re into tile row s*2UP + u, Im into row s*2UP + UP + u
     unsigned char *tile = tiles + buf * TILE_BYTES;
-    for (int item = tid; item < 128 * 8; item += NT) {
-      const int g8 = item >> 7, m = item & 127;
-      const int s = m / (2 * UP), r = m - s * (2 * UP);
-      const int u = r < UP ? r : r - UP, part = r < UP ? 0 : 1;
-      float v[8];
+    for (int item = tid; item < 8 * NG * UP; item += NT) {
+      const int u = item % UP, s = (item / UP) % NG, g8 = item / (UP * NG);
+      const bool live = s < nact && u < U;
+      const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KC + 8 * g8) * U + u;
+      const int left = nr_s[s] - (c * KC + 8 * g8);
+      float2 v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int b = c * KC + 8 * g8 + j;  // antenna within the system
-        const int sc = s < NG ? s : 0;
-        const bool ok = s < nact && u < U && b < nr_s[sc];
-        const float *src = stage + (size_t)sc * KC * 2 * U + (size_t)(8 * g8 + j) * 2 * U;
-        v[j] = ok ? src[2 * u + part] : 0.f;
-      }
-      uint4 q;
-      q.x = tc::pack2<BF16>(v[0], v[1]);
-      q.y = tc::pack2<BF16>(v[2], v[3]);
-      q.z = tc::pack2<BF16>(v[4], v[5]);
-      q.w = tc::pack2<BF16>(v[6], v[7]);
-      *reinterpret_cast<uint4 *>(tile + tc::sw128_offset(m, g8)) = q;
+      for (int j = 0; j < 8; ++j)
+        v[j] = (live && j < left) ? __ldg(src + (size_t)j * U) : make_float2(0.f, 0.f);
+      uint4 re, im;
+      re.x = tc::pack2<BF16>(v[0].x, v[1].x);
+      re.y = tc::pack2<BF16>(v[2].x, v[3].x);
+      re.z = tc::pack2<BF16>(v[4].x, v[5].x);
+      re.w = tc::pack2<BF16>(v[6].x, v[7].x);
+      im.x = tc::pack2<BF16>(v[0].y, v[1].y);
+      im.y = tc::pack2<BF16>(v[2].y, v[3].y);
+      im.z = tc::pack2<BF16>(v[4].y, v[5].y);
+      im.w = tc::pack2<BF16>(v[6].y, v[7].y);
+      *reinterpret_cast<uint4 *>(tile + tc::sw128_offset(s * M2 + u, g8)) = re;
+      *reinterpret_cast<uint4 *>(tile + tc::sw128_offset(s * M2 + UP + u, g8)) = im;
     }
     fence_proxy_async_smem();
     __syncthreads();
@@ -220,17 +200,17 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
       tc::commit(bar_mma + buf);
     }
   }
-  if (!timeout && nchunks > 0) {
+  if (ok && nchunks > 0) {
     const int last = nchunks - 1;
-    if (!mbar_wait(bar_mma + (last & 1), (last >> 1) & 1)) timeout = true;
+    ok = mbar_wait_cta(bar_mma + (last & 1), (last >> 1) & 1);
   }
-  timeout = __syncthreads_or(timeout) != 0;
   tc::fence_after_sync();
 
-  if (timeout) {  // let anything in flight land, free TMEM, report
-    mbar_wait(bar_tma, 0);
-    mbar_wait(bar_mma, 0);
-    mbar_wait(bar_mma + 1, 0);
+  if (!ok) {  // let anything in flight land, free TMEM, report
+    if (tid == 0) {
+      mbar_wait(bar_mma, 0);
+      mbar_wait(bar_mma + 1, 0);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -247,10 +227,10 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
     return;
   }
 
-  // ---- TMEM -> P (the diagonal 2UP x 2UP blocks) ---------------------------
+  // ---- TMEM -> P (the diagonal 2UP x 2UP blocks) ------------------------------
   if (warp < 4) {
     const int m = 32 * warp + lane;
-    const int s = m / (2 * UP), r = m - s * (2 * UP);
+    const int s = m / M2, r = m - s * M2;
 #pragma unroll
     for (int cc = 0; cc < 4; ++cc) {
       float v[32];
@@ -258,7 +238,7 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int n = 32 * cc + j;
-        if (s < NG && n / (2 * UP) == s) P[(size_t)s * 2 * UP * PS + r * PS + (n - s * 2 * UP)] = v[j];
+        if (s < NG && n / M2 == s) P[T::p_index(s, r, n - s * M2)] = v[j];
       }
     }
   }
@@ -269,32 +249,32 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
     tc::tmem_dealloc(taddr, TMEM_COLS);
   }
 
-  // ---- P -> G (Hermitian, lower triangle mirrored) -------------------------
+  // ---- P -> G (Hermitian, lower triangle mirrored) ------------------------------
   for (int e = tid; e < NG * UP * UP; e += NT) {
     const int s = e / (UP * UP), ij = e - s * UP * UP, i = ij / UP, j = ij - i * UP;
     float2 g = make_float2(0.f, 0.f);
     if (s < nact && i < U && j < U) {
-      const float *Pb = P + (size_t)s * 2 * UP * PS;
       const int a = i >= j ? i : j, b = i >= j ? j : i;  // lower-triangle source
-      g.x = Pb[a * PS + b] + Pb[(UP + a) * PS + UP + b];
-      g.y = (a == b) ? 0.f : Pb[(UP + a) * PS + b] - Pb[a * PS + UP + b];
+      g.x = P[T::p_index(s, a, b)] + P[T::p_index(s, UP + a, UP + b)];
+      g.y = (a == b) ? 0.f : P[T::p_index(s, UP + a, b)] - P[T::p_index(s, a, UP + b)];
       if (i < j) g.y = -g.y;
     }
     Gs[e] = g;
   }
   __syncthreads();
-  // per-system finiteness of G (covers H) and of the symbols: a NaN of one
-  // system must not fail the others
+  // per-system finiteness of G (covers H) and of the symbols
   if (warp < NG) {
-    bool ok = true;
-    for (int e = lane; e < UP * UP; e += 32) ok = ok && cfinite(Gs[warp * UP * UP + e]);
-    for (int e = lane; e < K * UP; e += 32) ok = ok && cfinite(Ss[warp * K * UP + e]);
-    ok = __all_sync(FULL, ok);
-    if (lane == 0) st_s[warp] = ok ? ST_OK : ST_NONFINITE;
+    bool fin = true;
+    for (int e = lane; e < UP * UP; e += 32) fin = fin && cfinite(Gs[warp * UP * UP + e]);
+    for (int e = lane; e < K * UP; e += 32) fin = fin && cfinite(Ss[warp * K * UP + e]);
+    fin = __all_sync(FULL, fin);
+    if (lane == 0) st_s[warp] = fin ? ST_OK : ST_NONFINITE;
   }
+  // the region is free again: zero the pads of the apply rows
+  zero_row_pads<UP>(stage, NG * KA, U, tid);
   __syncthreads();
 
-  // ---- solve: one warp per system ------------------------------------------
+  // ---- solve: one warp per system --------------------------------------------
   if (warp < nact) {
     float sc = 0.f;
     const int st = warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP, Zs + warp * K * UP, UP,
@@ -305,23 +285,22 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
       sc_s[warp] = sc;
     }
   }
-  __syncthreads();
-
-  // ---- apply: rows re-fetched (L2) into padded staging, thread per row ------
-  zero_row_pads<UP>(stage, NG * KC, U, tid);
   fence_proxy_async_smem();
   __syncthreads();
-  for (int c = 0; c < nchunks; ++c) {
+
+  // ---- apply: rows bulk-copied again (L2) into padded rows -------------------
+  const int achunks = (kmax + KA - 1) / KA;
+  const int Kh = (K + 1) / 2;  // two threads per row, each half of the symbols
+  for (int c = 0; c < achunks && ok; ++c) {
     if (c > 0) {
-      __syncthreads();
       fence_proxy_async_smem();
+      __syncthreads();  // previous rows consumed
     }
     if (tma) {
       if (warp == 0) {
         uint32_t bytes = 0;
-#pragma unroll
         for (int s = 0; s < NG; ++s) {
-          const int m = min(KC, nr_s[s] - c * KC);
+          const int m = min(KA, nr_s[s] - c * KA);
           if (m > 0 && st_s[s] == ST_OK) bytes += (uint32_t)m * U * 8u;
         }
         if (lane == 0) {
@@ -330,66 +309,56 @@ __global__ void __launch_bounds__(NT) k_fused_tc(SysDesc d, const float2 *__rest
         }
         __syncwarp();
         for (int s = 0; s < NG; ++s) {
-          const int m = min(KC, nr_s[s] - c * KC);
+          const int m = min(KA, nr_s[s] - c * KA);
           if (m <= 0 || st_s[s] != ST_OK) continue;
-          const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KC) * U;
+          const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KA) * U;
           for (int r = lane; r < m; r += 32)
-            tma_load_1d(stage + ((size_t)s * KC + r) * RS, src + (size_t)r * U, (uint32_t)U * 8u,
+            tma_load_1d(stage + ((size_t)s * KA + r) * RS, src + (size_t)r * U, (uint32_t)U * 8u,
                         bar_tma);
         }
       }
-      if (!mbar_wait(bar_tma, (nchunks + c) & 1)) timeout = true;
+      ok = mbar_wait_cta(bar_tma, c & 1);
+      if (!ok) {
+        if (tid == 0) mbar_wait(bar_tma, c & 1);
+        __syncthreads();
+        break;
+      }
     } else {
       for (int s = 0; s < NG; ++s) {
-        const int m = min(KC, nr_s[s] - c * KC);
+        const int m = min(KA, nr_s[s] - c * KA);
         if (m <= 0 || st_s[s] != ST_OK) continue;
-        const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KC) * U;
+        const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KA) * U;
         for (int e = tid; e < m * U; e += NT) {
           const int r = e / U, u = e - r * U;
-          *reinterpret_cast<float2 *>(stage + ((size_t)s * KC + r) * RS + 2 * u) = __ldg(src + e);
+          *reinterpret_cast<float2 *>(stage + ((size_t)s * KA + r) * RS + 2 * u) = __ldg(src + e);
         }
       }
+      __syncthreads();
     }
-    if (__syncthreads_or(timeout)) {
-      mbar_wait(bar_tma, (nchunks + c) & 1);
-      break;
-    }
-    for (int e = tid; e < NG * KC; e += NT) {
-      const int s = e / KC, r = e - s * KC;
-      const int b = c * KC + r;
-      if (s >= nact || b >= nr_s[s]) continue;
-      float2 *Xn = X + (size_t)n_s[s] * K * d.B;
+    // two rows (b, b + KA/2) and half of the symbols per thread: each
+    // broadcast z load feeds both rows
+    constexpr int RP = KA / 2;
+    for (int e = tid; e < NG * RP * 2; e += NT) {
+      const int half = e & 1, rp = (e >> 1) % RP, s = (e >> 1) / RP;
+      const int b0 = c * KA + rp, b1 = b0 + RP;
+      if (s >= nact || b0 >= nr_s[s]) continue;
+      const bool has1 = b1 < nr_s[s];
+      float2 *Xn = X + (size_t)n_s[s] * K * d.B + lo_s[s];
+      const int k0 = half * Kh, k1 = min(K, k0 + Kh);
       if (st_s[s] != ST_OK) {
-        for (int k = 0; k < K; ++k) Xn[(size_t)k * d.B + lo_s[s] + b] = make_float2(0.f, 0.f);
+        for (int k = k0; k < k1; ++k) {
+          Xn[(size_t)k * d.B + b0] = make_float2(0.f, 0.f);
+          if (has1) Xn[(size_t)k * d.B + b1] = make_float2(0.f, 0.f);
+        }
         continue;
       }
-      const float *hrow = stage + ((size_t)s * KC + r) * RS;
-      const float2 *zs = Zs + s * K * UP;
-      const float scl = sc_s[s];
-      for (int kb = 0; kb < K; kb += 7) {
-        float2 acc[7];
-#pragma unroll
-        for (int kk = 0; kk < 7; ++kk) acc[kk] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < UP; u += 2) {
-          const float4 h = *reinterpret_cast<const float4 *>(hrow + 2 * u);
-          const float2 h0 = make_float2(h.x, h.y), h1 = make_float2(h.z, h.w);
-#pragma unroll
-          for (int kk = 0; kk < 7; ++kk) {
-            if (kb + kk < K) {
-              const float4 z = *reinterpret_cast<const float4 *>(zs + (kb + kk) * UP + u);
-              cmac_cj(acc[kk], h0, make_float2(z.x, z.y));
-              cmac_cj(acc[kk], h1, make_float2(z.z, z.w));
-            }
-          }
-        }
-#pragma unroll
-        for (int kk = 0; kk < 7; ++kk)
-          if (kb + kk < K) Xn[(size_t)(kb + kk) * d.B + lo_s[s] + b] = cscale(acc[kk], scl);
-      }
+      const float *hrow[2] = {stage + ((size_t)s * KA + rp) * RS,
+                              stage + ((size_t)s * KA + rp + RP) * RS};
+      float2 *xcol[2] = {Xn + b0, Xn + b1};
+      apply_rows_k<UP, 2>(hrow, has1 ? 2 : 1, Zs + s * K * UP, k0, k1, sc_s[s], xcol, d.B);
     }
   }
-  if (timeout) {
+  if (!ok) {
     for (int s = 0; s < nact; ++s) {
       zero_rows<UP>(nr_s[s], K, X + (size_t)n_s[s] * K * d.B, d.B, lo_s[s], tid);
       if (tid == 0) st_s[s] = ST_TIMEOUT;
