@@ -142,6 +142,46 @@ dp_status dp_precode(dp_plan_t plan, const void *H, const void *S, void *X);
  * Returns the first non-DP_OK entry (DP_OK if all succeeded). */
 dp_status dp_status_get(dp_plan_t plan, int *host_status);
 
+/* ---- Batched uneven precoding ---------------------------------------------
+ * The paper aggregates the N_sc subcarriers x K symbols of a slot into one
+ * batch to fill the GPU (Sec. IV-B); a batch here goes further and runs n
+ * independent instances of uneven size (each its own dp_plan_desc: users,
+ * antennas, clusters, subcarriers, mode, precision) in persistent launches.
+ * Instances are bucketed by kernel family and padded user count: the
+ * tensor-core family (prec BF16/FP16 with U <= 32), the FP32 family with the
+ * antenna block resident in shared memory, and a streaming remainder;
+ * instances with prec BF16/FP16 and U > 32 run the FP32 path (more accurate
+ * than requested).  Each bucket is one persistent launch whose CTAs pull
+ * work items from an atomic queue, largest first; the bucket launches are
+ * captured once into a CUDA graph (on a non-NULL stream) and replayed on
+ * every call.  Per-instance outputs and status follow the single-plan
+ * conventions.
+ *
+ * dp_batch_create: validate and copy the n descriptions (as dp_plan_create
+ *   does, same error codes), build the work lists and allocate the batch's
+ *   workspace on the current device.  stream: where the batch enqueues.
+ * dp_batch_precode: H[i], S[i], X[i] are host arrays of n device pointers to
+ *   instance i's H [n_sc][B][U], S [n_sc][K][U] and X [n_sc][K][B] (layouts
+ *   and alignment as above).  Asynchronous; the pointer table is copied
+ *   before the call returns.
+ * dp_batch_tune: autotuner.  Runs every bucket at each feasible number of
+ *   CTAs per SM (trials timed runs each, after one warm-up) on the given
+ *   arrays, keeps the fastest, and rebuilds the graph.  Synchronous.
+ * dp_batch_status_get: waits, then writes the per-subcarrier status of every
+ *   instance, instance after instance, into host_status (sum of n_sc entries;
+ *   NULL allowed) and returns the first failure.
+ * dp_batch_describe: a JSON string (owned by the batch) with the buckets,
+ *   their work items and the chosen CTAs per SM. */
+typedef struct dp_batch *dp_batch_t;
+dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, dp_batch_t *out);
+dp_status dp_batch_destroy(dp_batch_t b);
+dp_status dp_batch_precode(dp_batch_t b, const void *const *H, const void *const *S,
+                           void *const *X);
+dp_status dp_batch_tune(dp_batch_t b, const void *const *H, const void *const *S, void *const *X,
+                        int trials);
+dp_status dp_batch_status_get(dp_batch_t b, int *host_status);
+const char *dp_batch_describe(dp_batch_t b);
+
 /* Allocation-free precoding (the paper has no counterpart: this is a
  * deployment variant of dp_precode).  For callers that cannot call
  * cudaMalloc: a baseband runtime whose device memory is carved up once at

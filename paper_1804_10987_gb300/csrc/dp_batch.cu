@@ -1,0 +1,475 @@
+// dp_batch.cu -- batched precoding of many instances of uneven size (users,
+// antennas, clusters, subcarriers, mode, precision) in persistent launches.
+//
+// The instances are sorted into buckets by kernel family and padded user
+// count: the tensor-core family (BF16/FP16 Gram, <= 32 users), the FP32
+// fused family (antenna block resident in shared memory) and a streaming
+// remainder (instances whose blocks do not fit: Gram, solve and apply
+// kernels per instance).  Every bucket is one persistent launch whose CTAs
+// pull work items (a group of systems of one instance) from an atomic queue,
+// largest items first.  The launch sequence is captured once into a CUDA
+// graph and replayed; per call only the table of device pointers is
+// uploaded.  dp_batch_tune times each bucket at every feasible CTAs-per-SM
+// count and keeps the fastest.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/dprecode.h"
+#include "dp_internal.h"
+
+namespace {
+
+enum Family { FAM_TC = 0, FAM_FUSED = 1, FAM_STREAM = 2 };
+
+struct Bucket {
+  int family;
+  int UP;
+  bool bf16;
+  int Kmax = 0;
+  int maxrows = 0;
+  std::vector<dp::WorkItem> items;
+  dp::WorkItem *d_items = nullptr;
+  int max_blocks = 1;   // occupancy limit per SM
+  int blocks = 1;       // chosen CTAs per SM
+  float tuned_ms = -1.f;
+};
+
+struct Inst {
+  dp_plan_desc d;
+  std::vector<int> off;
+  int UP, nsys, maxrows, family;
+  bool bf16;
+  size_t status_off;  // offset of this instance's status block in the batch array
+  // workspace of the streaming family
+  float2 *w_G = nullptr, *w_Z = nullptr;
+  float *w_scale = nullptr;
+  int *d_off = nullptr;
+};
+
+bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+dp_status validate(const dp_plan_desc &d, std::vector<int> &off) {
+  if (d.U < 1 || d.U > 64 || d.B < 1 || d.B > 4096 || d.C < 1 || d.C > d.B || d.n_sc < 0 ||
+      d.K < 0 || d.K > 64)
+    return DP_ERR_INVALID_ARG;
+  if (d.mode != DP_ZF && d.mode != DP_WF && d.mode != DP_FDWF) return DP_ERR_INVALID_ARG;
+  if (d.prec != DP_FP32 && d.prec != DP_BF16 && d.prec != DP_FP16) return DP_ERR_INVALID_ARG;
+  if (!(d.rho2 > 0.f) || !std::isfinite(d.rho2) || !(d.Es > 0.f) || !std::isfinite(d.Es) ||
+      !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
+    return DP_ERR_INVALID_ARG;
+  if (d.refine != 0) return DP_ERR_UNSUPPORTED;
+  off.assign(d.C + 1, 0);
+  for (int c = 0; c < d.C; ++c) {
+    int bc;
+    if (d.cluster_sizes) {
+      bc = d.cluster_sizes[c];
+    } else {
+      if (d.B % d.C) return DP_ERR_PARTITION;
+      bc = d.B / d.C;
+    }
+    if (bc < 1) return DP_ERR_PARTITION;
+    off[c + 1] = off[c] + bc;
+  }
+  if (off[d.C] != d.B) return DP_ERR_PARTITION;
+  int minbc = d.B;
+  for (int c = 0; c < d.C; ++c) minbc = std::min(minbc, off[c + 1] - off[c]);
+  if ((d.mode == DP_ZF || (d.mode == DP_WF && d.N0 == 0.f)) && d.B < d.U)
+    return DP_ERR_UNSUPPORTED;
+  if (d.mode == DP_FDWF && (double)d.tau * d.U * d.N0 * d.C / d.rho2 == 0.0 && minbc < d.U)
+    return DP_ERR_UNSUPPORTED;
+  return DP_OK;
+}
+
+dp::SysDesc sys_of(const Inst &in, const void *H) {
+  dp::SysDesc s{};
+  const dp_plan_desc &d = in.d;
+  s.U = d.U;
+  s.B = d.B;
+  s.K = d.K;
+  s.n_sc = d.n_sc;
+  s.nsys = in.nsys;
+  s.off = in.d_off;
+  s.Es = d.Es;
+  const double U = d.U, N0 = d.N0, rho2 = d.rho2, C = d.C;
+  if (d.mode == DP_ZF) {
+    s.kappa = 0.f;
+    s.rho2_sys = d.rho2;
+  } else if (d.mode == DP_WF) {
+    s.kappa = (float)(U * N0 / rho2);
+    s.rho2_sys = d.rho2;
+  } else {
+    s.kappa = (float)(d.tau * U * N0 / (rho2 / C));
+    s.rho2_sys = (float)(rho2 / C);
+  }
+  s.tma_ok = (d.U % 2 == 0) && (H == nullptr || a16(H));
+  return s;
+}
+
+}  // namespace
+
+struct dp_batch {
+  int device = 0, n_sm = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<Inst> insts;
+  std::vector<Bucket> buckets;
+  std::vector<int> streaming;            // instances of the streaming family
+  dp::InstDesc *d_insts = nullptr;        // device table, rewritten every call
+  std::vector<dp::InstDesc> h_insts;
+  int *d_queues = nullptr;                // one counter per bucket
+  int *d_status = nullptr;
+  size_t status_len = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string info;
+};
+
+namespace {
+
+void free_batch(dp_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto &bk : b->buckets) cudaFree(bk.d_items);
+  for (auto &in : b->insts) {
+    cudaFree(in.w_G);
+    cudaFree(in.w_Z);
+    cudaFree(in.w_scale);
+    cudaFree(in.d_off);
+  }
+  cudaFree(b->d_insts);
+  cudaFree(b->d_queues);
+  cudaFree(b->d_status);
+  cudaGetLastError();
+  delete b;
+}
+
+// Enqueue bucket k (queue reset + persistent launch).
+cudaError_t enqueue_bucket(dp_batch *b, int k, cudaStream_t s) {
+  Bucket &bk = b->buckets[k];
+  if (bk.items.empty()) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(b->d_queues + k, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min<int>(bk.blocks * b->n_sm, (int)bk.items.size()));
+  if (bk.family == FAM_TC)
+    return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, (int)bk.items.size(),
+                               b->d_queues + k, bk.Kmax, grid, s);
+  return dp::launch_batch_fused(bk.UP, b->d_insts, bk.d_items, (int)bk.items.size(),
+                                b->d_queues + k, bk.maxrows, bk.Kmax, grid, s);
+}
+
+cudaError_t enqueue_streaming(dp_batch *b, int i, cudaStream_t s) {
+  Inst &in = b->insts[i];
+  const dp::InstDesc &t = b->h_insts[i];
+  if (in.d.n_sc == 0) return cudaSuccess;
+  cudaError_t e = dp::launch_gram(t.d, in.UP, t.H, in.w_G, s);
+  if (e == cudaSuccess) e = dp::launch_solve(t.d, in.UP, in.w_G, t.S, in.w_Z, in.w_scale, t.status, s);
+  if (e == cudaSuccess && in.d.K > 0) e = dp::launch_apply(t.d, in.UP, t.H, in.w_Z, in.w_scale, t.X, s);
+  return e;
+}
+
+// The persistent bucket launches (the part a graph captures: they read every
+// pointer from the device table, so the graph is independent of the call).
+cudaError_t enqueue_buckets(dp_batch *b, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < b->buckets.size() && e == cudaSuccess; ++k) e = enqueue_bucket(b, (int)k, s);
+  return e;
+}
+
+// Streaming instances take their pointers as kernel arguments: enqueued
+// eagerly on every call.
+cudaError_t enqueue_streams(dp_batch *b, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (size_t j = 0; j < b->streaming.size() && e == cudaSuccess; ++j)
+    e = enqueue_streaming(b, b->streaming[j], s);
+  return e;
+}
+
+// Write the pointer table for this call (host copy + upload on the stream).
+dp_status upload_table(dp_batch *b, const void *const *H, const void *const *S, void *const *X) {
+  for (size_t i = 0; i < b->insts.size(); ++i) {
+    const Inst &in = b->insts[i];
+    const bool empty = in.d.n_sc == 0, k0 = in.d.K == 0;
+    if (!empty && (!H[i] || !a16(H[i]))) return DP_ERR_INVALID_ARG;
+    if (!empty && !k0 && (!S[i] || !a16(S[i]) || !X[i] || !a16(X[i]))) return DP_ERR_INVALID_ARG;
+    dp::InstDesc &t = b->h_insts[i];
+    t.d = sys_of(in, H[i]);
+    t.H = static_cast<const float2 *>(H[i]);
+    t.S = static_cast<const float2 *>(S[i]);
+    t.X = static_cast<float2 *>(X[i]);
+    t.status = b->d_status + in.status_off;
+    t.scale_out = nullptr;
+  }
+  if (cudaMemcpyAsync(b->d_insts, b->h_insts.data(), sizeof(dp::InstDesc) * b->h_insts.size(),
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return DP_ERR_CUDA;
+  return DP_OK;
+}
+
+dp_status build_graph(dp_batch *b) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (b->graph) {
+    cudaGraphDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  if (b->stream == nullptr) return DP_OK;  // the legacy stream cannot be captured: run eagerly
+  if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return DP_OK;
+  }
+  cudaError_t e = enqueue_buckets(b, b->stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return DP_ERR_CUDA;
+  }
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    b->exec = nullptr;
+    return DP_ERR_CUDA;
+  }
+  b->graph = g;
+  return DP_OK;
+}
+
+void describe(dp_batch *b) {
+  std::string s = "{\"buckets\": [";
+  for (size_t k = 0; k < b->buckets.size(); ++k) {
+    const Bucket &bk = b->buckets[k];
+    char buf[256];
+    std::snprintf(buf, sizeof buf,
+                  "%s{\"family\": \"%s\", \"users_padded\": %d, \"items\": %zu, "
+                  "\"ctas_per_sm\": %d, \"max_ctas_per_sm\": %d, \"tuned_ms\": %.4f}",
+                  k ? ", " : "",
+                  bk.family == FAM_TC ? (bk.bf16 ? "tc_bf16" : "tc_fp16") : "fp32_fused", bk.UP,
+                  bk.items.size(), bk.blocks, bk.max_blocks, bk.tuned_ms);
+    s += buf;
+  }
+  char tail[64];
+  std::snprintf(tail, sizeof tail, "], \"streaming_instances\": %zu}", b->streaming.size());
+  s += tail;
+  b->info = s;
+}
+
+}  // namespace
+
+extern "C" {
+
+dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, dp_batch_t *out) {
+  if (!out) return DP_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!descs || n < 1) return DP_ERR_INVALID_ARG;
+  dp_batch *b = new (std::nothrow) dp_batch;
+  if (!b) return DP_ERR_OOM;
+  b->stream = reinterpret_cast<cudaStream_t>(stream);
+  b->insts.resize(n);
+  std::map<std::tuple<int, int, int>, int> bucket_of;
+  size_t status_len = 0;
+  for (int i = 0; i < n; ++i) {
+    Inst &in = b->insts[i];
+    in.d = descs[i];
+    dp_status st = validate(in.d, in.off);
+    if (st != DP_OK) {
+      delete b;
+      return st;
+    }
+    in.d.cluster_sizes = nullptr;
+    in.UP = dp::padded_users(in.d.U);
+    in.nsys = in.d.mode == DP_FDWF ? in.d.C : 1;
+    int maxbc = 0;
+    for (int c = 0; c < in.d.C; ++c) maxbc = std::max(maxbc, in.off[c + 1] - in.off[c]);
+    in.maxrows = in.d.mode == DP_FDWF ? maxbc : in.d.B;
+    in.bf16 = in.d.prec == DP_BF16;
+    if (in.d.prec != DP_FP32 && dp::tc_supported(in.UP)) in.family = FAM_TC;
+    else if (dp::fused_smem_bytes(in.UP, in.maxrows, in.d.K) != 0) in.family = FAM_FUSED;
+    else in.family = FAM_STREAM;
+    in.status_off = status_len;
+    status_len += (size_t)in.d.n_sc * in.nsys;
+  }
+  if (cudaGetDevice(&b->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return DP_ERR_CUDA;
+  }
+  b->status_len = status_len;
+  bool oom = cudaMalloc(&b->d_status, sizeof(int) * std::max<size_t>(1, status_len)) != cudaSuccess ||
+             cudaMalloc(&b->d_insts, sizeof(dp::InstDesc) * n) != cudaSuccess;
+  if (!oom) cudaMemset(b->d_status, 0, sizeof(int) * std::max<size_t>(1, status_len));
+  // cluster offsets and work items
+  for (int i = 0; i < n && !oom; ++i) {
+    Inst &in = b->insts[i];
+    oom = cudaMalloc(&in.d_off, sizeof(int) * in.off.size()) != cudaSuccess;
+    if (oom) break;
+    cudaMemcpy(in.d_off, in.off.data(), sizeof(int) * in.off.size(), cudaMemcpyHostToDevice);
+    const int nsys_total = in.d.n_sc * in.nsys;
+    if (nsys_total == 0) continue;
+    if (in.family == FAM_STREAM) {
+      b->streaming.push_back(i);
+      oom = cudaMalloc(&in.w_G, sizeof(float2) * nsys_total * in.d.U * in.d.U) != cudaSuccess ||
+            cudaMalloc(&in.w_Z, sizeof(float2) * nsys_total * std::max(1, in.d.K) * in.d.U) !=
+                cudaSuccess ||
+            cudaMalloc(&in.w_scale, sizeof(float) * nsys_total) != cudaSuccess;
+      continue;
+    }
+    auto key = std::make_tuple(in.family, in.UP, in.family == FAM_TC ? (int)in.bf16 : 0);
+    auto it = bucket_of.find(key);
+    int k;
+    if (it == bucket_of.end()) {
+      k = (int)b->buckets.size();
+      bucket_of[key] = k;
+      Bucket bk;
+      bk.family = in.family;
+      bk.UP = in.UP;
+      bk.bf16 = in.family == FAM_TC && in.bf16;
+      b->buckets.push_back(bk);
+    } else {
+      k = it->second;
+    }
+    Bucket &bk = b->buckets[k];
+    bk.Kmax = std::max(bk.Kmax, in.d.K);
+    bk.maxrows = std::max(bk.maxrows, in.maxrows);
+    const int per = in.family == FAM_TC ? dp::tc_systems_per_group(in.UP) : 1;
+    for (int s0 = 0; s0 < nsys_total; s0 += per)
+      bk.items.push_back(dp::WorkItem{i, s0, std::min(per, nsys_total - s0)});
+  }
+  if (oom) {
+    free_batch(b);
+    return DP_ERR_OOM;
+  }
+  // largest items first (antenna rows of the item's systems), so that the
+  // queue's tail is made of small items
+  for (auto &bk : b->buckets) {
+    auto cost = [&](const dp::WorkItem &w) {
+      const Inst &in = b->insts[w.inst];
+      return (long long)in.maxrows * in.UP * w.nact;
+    };
+    std::stable_sort(bk.items.begin(), bk.items.end(),
+                     [&](const dp::WorkItem &a, const dp::WorkItem &c) { return cost(a) > cost(c); });
+    if (cudaMalloc(&bk.d_items, sizeof(dp::WorkItem) * bk.items.size()) != cudaSuccess) {
+      free_batch(b);
+      return DP_ERR_OOM;
+    }
+    cudaMemcpy(bk.d_items, bk.items.data(), sizeof(dp::WorkItem) * bk.items.size(),
+               cudaMemcpyHostToDevice);
+    bk.max_blocks = bk.family == FAM_TC ? dp::tc_max_blocks_per_sm(bk.UP, bk.bf16, bk.Kmax)
+                                        : dp::fused_max_blocks_per_sm(bk.UP, bk.maxrows, bk.Kmax);
+    if (bk.max_blocks < 1) {
+      free_batch(b);
+      return DP_ERR_UNSUPPORTED;
+    }
+    bk.blocks = bk.max_blocks;
+  }
+  if (cudaMalloc(&b->d_queues, sizeof(int) * std::max<size_t>(1, b->buckets.size())) != cudaSuccess) {
+    free_batch(b);
+    return DP_ERR_OOM;
+  }
+  b->h_insts.resize(n);
+  for (int i = 0; i < n; ++i) b->h_insts[i] = dp::InstDesc{sys_of(b->insts[i], nullptr), nullptr,
+                                                           nullptr, nullptr,
+                                                           b->d_status + b->insts[i].status_off,
+                                                           nullptr};
+  describe(b);
+  *out = b;
+  return DP_OK;
+}
+
+dp_status dp_batch_destroy(dp_batch_t b) {
+  if (!b) return DP_ERR_INVALID_ARG;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+  return DP_OK;
+}
+
+dp_status dp_batch_precode(dp_batch_t b, const void *const *H, const void *const *S,
+                           void *const *X) {
+  if (!b || !H || !S || !X) return DP_ERR_INVALID_ARG;
+  if (cudaSetDevice(b->device) != cudaSuccess) return DP_ERR_CUDA;
+  if (dp_status st = upload_table(b, H, S, X)) return st;
+  if (!b->exec && b->stream != nullptr) {
+    if (dp_status st = build_graph(b)) return st;
+  }
+  cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, b->stream) : enqueue_buckets(b, b->stream);
+  if (e == cudaSuccess) e = enqueue_streams(b, b->stream);
+  return e == cudaSuccess ? DP_OK : DP_ERR_CUDA;
+}
+
+dp_status dp_batch_tune(dp_batch_t b, const void *const *H, const void *const *S, void *const *X,
+                        int trials) {
+  if (!b || !H || !S || !X || trials < 1) return DP_ERR_INVALID_ARG;
+  if (cudaSetDevice(b->device) != cudaSuccess) return DP_ERR_CUDA;
+  if (dp_status st = upload_table(b, H, S, X)) return st;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return DP_ERR_CUDA;
+  dp_status rc = DP_OK;
+  for (size_t k = 0; k < b->buckets.size() && rc == DP_OK; ++k) {
+    Bucket &bk = b->buckets[k];
+    if (bk.items.empty()) continue;
+    float best = 1e30f;
+    int best_blocks = bk.max_blocks;
+    for (int c = 1; c <= bk.max_blocks && rc == DP_OK; ++c) {
+      bk.blocks = c;
+      float sum = 0.f;
+      for (int t = 0; t <= trials && rc == DP_OK; ++t) {  // first run warms up
+        cudaEventRecord(e0, b->stream);
+        if (enqueue_bucket(b, (int)k, b->stream) != cudaSuccess) rc = DP_ERR_CUDA;
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = DP_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (t > 0) sum += ms;
+      }
+      const float ms = sum / trials;
+      if (ms < best) {
+        best = ms;
+        best_blocks = c;
+      }
+    }
+    bk.blocks = best_blocks;
+    bk.tuned_ms = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != DP_OK) return rc;
+  describe(b);
+  return build_graph(b);
+}
+
+const char *dp_batch_describe(dp_batch_t b) { return b ? b->info.c_str() : ""; }
+
+dp_status dp_batch_status_get(dp_batch_t b, int *host_status) {
+  if (!b) return DP_ERR_INVALID_ARG;
+  if (cudaSetDevice(b->device) != cudaSuccess) return DP_ERR_CUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DP_ERR_CUDA;
+  std::vector<int> sys(std::max<size_t>(1, b->status_len));
+  if (b->status_len &&
+      cudaMemcpy(sys.data(), b->d_status, sizeof(int) * b->status_len, cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+    return DP_ERR_CUDA;
+  dp_status first = DP_OK;
+  size_t o = 0;
+  for (const Inst &in : b->insts) {
+    for (int n = 0; n < in.d.n_sc; ++n) {
+      int worst = 0;
+      for (int g = 0; g < in.nsys; ++g) worst = std::max(worst, sys[in.status_off + (size_t)n * in.nsys + g]);
+      if (host_status) host_status[o] = worst;
+      ++o;
+      if (first == DP_OK && worst) first = static_cast<dp_status>(worst);
+    }
+  }
+  return first;
+}
+
+}  // extern "C"

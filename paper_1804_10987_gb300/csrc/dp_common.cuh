@@ -138,6 +138,25 @@ struct SysDesc {
   int tma_ok;       // rows may be fetched with 1-D bulk copies
 };
 
+// One precoding instance: its systems and its device arrays (H [n_sc][B][U],
+// S [n_sc][K][U], X [n_sc][K][B], status [n_sc * nsys], optional scale).
+struct InstDesc {
+  SysDesc d;
+  const float2 *H;
+  const float2 *S;
+  float2 *X;
+  int *status;
+  float *scale_out;
+};
+
+// A unit of work of a persistent kernel: systems [sys0, sys0 + nact) of
+// instance inst.
+struct WorkItem {
+  int inst;
+  int sys0;
+  int nact;
+};
+
 __device__ __forceinline__ void sys_rows(const SysDesc &d, int g, int &lo, int &hi) {
   if (d.nsys == 1) {
     lo = 0;

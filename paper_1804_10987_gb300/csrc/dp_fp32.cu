@@ -261,16 +261,22 @@ __global__ void __launch_bounds__(NT) k_apply(SysDesc d, const float2 *__restric
   }
 }
 
-// ----------------------------------------------------------------- fused ---
 template <int UP>
-__global__ void __launch_bounds__(NT) k_fused(SysDesc d, const float2 *__restrict__ H,
-                                              const float2 *__restrict__ S,
-                                              float2 *__restrict__ X, int *__restrict__ status,
-                                              float *__restrict__ scale_out, int maxrows) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+__host__ __device__ constexpr size_t fused_bar_offset(int maxrows, int K) {
+  return (size_t)maxrows * Geo<UP>::RS * 4 + 2 * (size_t)UP * UP * 8 + 2 * (size_t)K * UP * 8 +
+         16 * 4;
+}
+
+// ----------------------------------------------------------------- fused ---
+// One system with its antenna block resident in shared memory.  tma_waits
+// counts the phases of bar consumed by this CTA so far (persistent CTAs run
+// many systems).  Returns false if the bounded wait for the rows gave up.
+template <int UP>
+__device__ bool fused_system(const InstDesc &in, int sys, unsigned char *smem_raw, int maxrows,
+                             int Kmax, uint64_t *bar, uint32_t &tma_waits) {
   constexpr int RS = Geo<UP>::RS;
+  const SysDesc &d = in.d;
   const int tid = threadIdx.x;
-  const int sys = blockIdx.x;
   const int n = sys / d.nsys, g = sys - n * d.nsys;
   int lo, hi;
   sys_rows(d, g, lo, hi);
@@ -280,33 +286,31 @@ __global__ void __launch_bounds__(NT) k_fused(SysDesc d, const float2 *__restric
   float2 *G = reinterpret_cast<float2 *>(Hs + (size_t)maxrows * RS);
   float2 *A = G + UP * UP;
   float2 *Ss = A + UP * UP;
-  float2 *Zs = Ss + K * UP;
-  float *red = reinterpret_cast<float *>(Zs + K * UP);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(red + 16);
-  float2 *Xn = X + (size_t)n * K * d.B;
+  float2 *Zs = Ss + Kmax * UP;
+  float *red = reinterpret_cast<float *>(Zs + Kmax * UP);
+  float2 *Xn = in.X + (size_t)n * K * d.B;
   const bool tma = d.tma_ok != 0;
 
   // a1 prologue: fetch this system's antenna block and the symbols
+  __syncthreads();  // the previous system is done with the buffers
   zero_row_pads<UP>(Hs, nrows, U, tid);
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
   fence_proxy_async_smem();
   __syncthreads();
-  fetch_rows<UP>(Hs, H + (size_t)n * d.B * U, lo, nrows, U, tma, bar, tid);
-  const bool sfin = load_symbols<UP>(S + (size_t)n * K * U, Ss, U, K, tid);
-  bool timeout = false;
-  if (tma) timeout = !mbar_wait_cta(bar, 0);
-  if (timeout) {
-    if (tid == 0) mbar_wait(bar, 0);
-    __syncthreads();
-    zero_rows<UP>(nrows, K, Xn, d.B, lo, tid);
-    if (tid == 0) {
-      report(status, sys, ST_TIMEOUT);
-      if (scale_out) scale_out[sys] = 0.f;
+  fetch_rows<UP>(Hs, in.H + (size_t)n * d.B * U, lo, nrows, U, tma, bar, tid);
+  const bool sfin = load_symbols<UP>(in.S + (size_t)n * K * U, Ss, U, K, tid);
+  if (tma) {
+    const bool ok = mbar_wait_cta(bar, tma_waits & 1);
+    ++tma_waits;
+    if (!ok) {
+      if (tid == 0) mbar_wait(bar, (tma_waits - 1) & 1);
+      __syncthreads();
+      zero_rows<UP>(nrows, K, Xn, d.B, lo, tid);
+      if (tid == 0) {
+        report(in.status, sys, ST_TIMEOUT);
+        if (in.scale_out) in.scale_out[sys] = 0.f;
+      }
+      return false;
     }
-    return;
   }
 
   // a1 + a2: Gram over all antennas of the system (the cluster sum is the
@@ -345,8 +349,46 @@ __global__ void __launch_bounds__(NT) k_fused(SysDesc d, const float2 *__restric
     zero_rows<UP>(nrows, K, Xn, d.B, lo, tid);
   }
   if (tid == 0) {
-    report(status, sys, st);
-    if (scale_out) scale_out[sys] = sc;
+    report(in.status, sys, st);
+    if (in.scale_out) in.scale_out[sys] = sc;
+  }
+  return true;
+}
+
+template <int UP>
+__global__ void __launch_bounds__(NT) k_fused(InstDesc in, int maxrows) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + fused_bar_offset<UP>(maxrows, in.d.K));
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  uint32_t waits = 0;
+  fused_system<UP>(in, blockIdx.x, smem_raw, maxrows, in.d.K, bar, waits);
+}
+
+// Persistent form over a work-item queue (one system per item).
+template <int UP>
+__global__ void __launch_bounds__(NT) k_batch_fused(const InstDesc *__restrict__ insts,
+                                                    const WorkItem *__restrict__ items,
+                                                    int n_items, int *__restrict__ queue,
+                                                    int maxrows, int Kmax) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int next;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + fused_bar_offset<UP>(maxrows, Kmax));
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  uint32_t waits = 0;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+    __syncthreads();
+    const int it = next;
+    if (it >= n_items) break;
+    const WorkItem w = items[it];
+    if (!fused_system<UP>(insts[w.inst], w.sys0, smem_raw, maxrows, Kmax, bar, waits)) break;
   }
 }
 
@@ -360,8 +402,7 @@ constexpr size_t kSmemCap = 220 * 1024;
 
 template <int UP>
 size_t fused_bytes_t(int maxrows, int K) {
-  return (size_t)maxrows * Geo<UP>::RS * 4 + 2 * (size_t)UP * UP * 8 + 2 * (size_t)K * UP * 8 +
-         16 * 4 + 16;
+  return fused_bar_offset<UP>(maxrows, K) + 16;
 }
 
 template <int UP>
@@ -410,8 +451,30 @@ cudaError_t launch_fused_t(const SysDesc &d, int maxrows, const float2 *H, const
   const size_t bytes = fused_bytes_t<UP>(maxrows, d.K);
   cudaError_t e = set_smem(k_fused<UP>, bytes);
   if (e != cudaSuccess) return e;
-  k_fused<UP><<<d.n_sc * d.nsys, NT, bytes, s>>>(d, H, S, X, status, scale_out, maxrows);
+  InstDesc in{d, H, S, X, status, scale_out};
+  k_fused<UP><<<d.n_sc * d.nsys, NT, bytes, s>>>(in, maxrows);
   return cudaGetLastError();
+}
+
+template <int UP>
+cudaError_t launch_batch_fused_t(const InstDesc *insts, const WorkItem *items, int n_items,
+                                 int *queue, int maxrows, int Kmax, int grid, cudaStream_t s) {
+  const size_t bytes = fused_bytes_t<UP>(maxrows, Kmax);
+  cudaError_t e = set_smem(k_batch_fused<UP>, bytes);
+  if (e != cudaSuccess) return e;
+  k_batch_fused<UP><<<grid, NT, bytes, s>>>(insts, items, n_items, queue, maxrows, Kmax);
+  return cudaGetLastError();
+}
+
+template <int UP>
+int fused_blocks_t(int maxrows, int Kmax) {
+  const size_t bytes = fused_bytes_t<UP>(maxrows, Kmax);
+  if (set_smem(k_batch_fused<UP>, bytes) != cudaSuccess) return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_fused<UP>, NT, bytes) !=
+      cudaSuccess)
+    return 0;
+  return n;
 }
 
 #define DP_DISPATCH_UP(UPV, CALL)                      \
@@ -473,6 +536,26 @@ cudaError_t launch_apply(const SysDesc &d, int UP, const float2 *H, const float2
 cudaError_t launch_fused(const SysDesc &d, int UP, int maxrows, const float2 *H, const float2 *S,
                          float2 *X, int *status, float *scale_out, cudaStream_t s) {
   DP_DISPATCH_UP(UP, (launch_fused_t<UPC>(d, maxrows, H, S, X, status, scale_out, s)));
+}
+
+cudaError_t launch_batch_fused(int UP, const InstDesc *insts, const WorkItem *items, int n_items,
+                               int *queue, int maxrows, int Kmax, int grid, cudaStream_t s) {
+  DP_DISPATCH_UP(UP, (launch_batch_fused_t<UPC>(insts, items, n_items, queue, maxrows, Kmax,
+                                                 grid, s)));
+}
+
+int fused_max_blocks_per_sm(int UP, int maxrows, int Kmax) {
+  switch (UP) {
+    case 8: return fused_blocks_t<8>(maxrows, Kmax);
+    case 16: return fused_blocks_t<16>(maxrows, Kmax);
+    case 24: return fused_blocks_t<24>(maxrows, Kmax);
+    case 32: return fused_blocks_t<32>(maxrows, Kmax);
+    case 40: return fused_blocks_t<40>(maxrows, Kmax);
+    case 48: return fused_blocks_t<48>(maxrows, Kmax);
+    case 56: return fused_blocks_t<56>(maxrows, Kmax);
+    case 64: return fused_blocks_t<64>(maxrows, Kmax);
+    default: return 0;
+  }
 }
 
 }  // namespace dp

@@ -27,10 +27,21 @@ cudaError_t launch_apply(const SysDesc &d, int UP, const float2 *H, const float2
                          const float *scale, float2 *X, cudaStream_t s);
 cudaError_t launch_fused(const SysDesc &d, int UP, int maxrows, const float2 *H, const float2 *S,
                          float2 *X, int *status, float *scale_out, cudaStream_t s);
+// Persistent FP32 fused kernel over a work-item queue (one system per item;
+// queue must be 0); maxrows / Kmax bound the bucket's systems.
+cudaError_t launch_batch_fused(int UP, const InstDesc *insts, const WorkItem *items, int n_items,
+                               int *queue, int maxrows, int Kmax, int grid, cudaStream_t s);
+int fused_max_blocks_per_sm(int UP, int maxrows, int Kmax);
 
 // Reduced-precision fused path (tensor-core Gram): users padded to <= 32.
 bool tc_supported(int UP);
 cudaError_t launch_fused_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
                             float2 *X, int *status, float *scale_out, cudaStream_t s);
+// Systems per work item of the tensor-core path (the CTA's group).
+int tc_systems_per_group(int UP);
+// Persistent tensor-core kernel over a work-item queue (queue must be 0).
+cudaError_t launch_batch_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
+                            int n_items, int *queue, int Kmax, int grid, cudaStream_t s);
+int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax);
 
 }  // namespace dp

@@ -77,16 +77,76 @@ __host__ __device__ TcSmem tc_smem_layout(int K) {
   return L;
 }
 
+// Per-CTA state of the tensor-core path, kept across the groups a persistent
+// CTA processes: shared-memory carve-up, TMEM base, and the number of phases
+// of each mbarrier consumed so far (every arrival is matched by one wait).
+struct TcCtx {
+  unsigned char *base;
+  TcSmem L;
+  uint32_t taddr;
+  uint32_t tma_waits;
+  uint32_t mma_commits[2];
+  uint32_t mma_waits[2];
+};
+
+template <int UP>
+__device__ __forceinline__ void tc_setup(TcCtx &cx, unsigned char *smem_raw, int Kmax) {
+  cx.base = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  cx.L = tc_smem_layout<UP>(Kmax);
+  cx.tma_waits = 0;
+  cx.mma_commits[0] = cx.mma_commits[1] = 0;
+  cx.mma_waits[0] = cx.mma_waits[1] = 0;
+  uint64_t *bar_tma = reinterpret_cast<uint64_t *>(cx.base + cx.L.bars);
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(cx.base + cx.L.tmem);
+  if (threadIdx.x == 0) {
+    mbar_init(bar_tma, 1);
+    mbar_init(bar_tma + 1, 1);
+    mbar_init(bar_tma + 2, 1);
+    fence_mbar_init();
+  }
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(tmem_holder, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  cx.taddr = *tmem_holder;
+}
+
+__device__ __forceinline__ void tc_teardown(TcCtx &cx) {
+  tc::fence_before_sync();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(cx.taddr, TMEM_COLS);
+  }
+}
+
+// Wait for the oldest outstanding commit of tile buffer buf (CTA-wide).
+__device__ __forceinline__ bool tc_wait_mma(TcCtx &cx, int buf) {
+  uint64_t *bar_mma = reinterpret_cast<uint64_t *>(cx.base + cx.L.bars) + 1;
+  const bool ok = mbar_wait_cta(bar_mma + buf, cx.mma_waits[buf] & 1);
+  ++cx.mma_waits[buf];
+  return ok;
+}
+
+// Systems [sys0, sys0 + nact) of one instance (nact <= NG): Gram on the tensor
+// cores, solve, apply.  Returns false if a bounded wait gave up (the
+// systems' outputs are then zeroed and their status set to ST_TIMEOUT).
 template <int UP, bool BF16>
-__global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
-    k_fused_tc(SysDesc d, const float2 *__restrict__ H, const float2 *__restrict__ S,
-               float2 *__restrict__ X, int *__restrict__ status, float *__restrict__ scale_out) {
+__device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   using T = TcGeo<UP>;
   constexpr int NG = T::NG, RS = T::RS, M2 = T::M2;
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char *base = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const TcSmem L = tc_smem_layout<UP>(d.K);
+  const SysDesc &d = in.d;
+  const float2 *__restrict__ H = in.H;
+  const float2 *__restrict__ S = in.S;
+  float2 *__restrict__ X = in.X;
+  int *__restrict__ status = in.status;
+  float *__restrict__ scale_out = in.scale_out;
+  const TcSmem &L = cx.L;
+  unsigned char *base = cx.base;
   unsigned char *tiles = base + L.region;
   float *P = reinterpret_cast<float *>(base + L.region);
   float *stage = reinterpret_cast<float *>(base + L.region);
@@ -99,17 +159,14 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
   int *nr_s = lo_s + NG;                                // antennas of each system
   int *n_s = nr_s + NG;                                 // subcarrier of each system
   uint64_t *bar_tma = reinterpret_cast<uint64_t *>(base + L.bars);
-  uint64_t *bar_mma = bar_tma + 1;  // two, one per tile
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(base + L.tmem);
+  const uint32_t taddr = cx.taddr;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int U = d.U, K = d.K;
-  const int total = d.n_sc * d.nsys;
-  const int sys0 = blockIdx.x * NG;
-  const int nact = min(NG, total - sys0);
   const bool tma = d.tma_ok != 0;
 
-  // ---- set-up: systems of the group, barriers, TMEM, symbols ---------------
+  // ---- systems of the group, symbols -----------------------------------------
+  __syncthreads();  // the previous group is done with every shared buffer
   if (tid < NG) {
     int lo = 0, hi = 0, n = 0;
     if (tid < nact) {
@@ -121,16 +178,6 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
     nr_s[tid] = hi - lo;
     n_s[tid] = n;
   }
-  if (tid == 0) {
-    mbar_init(bar_tma, 1);
-    mbar_init(bar_mma, 1);
-    mbar_init(bar_mma + 1, 1);
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    tc::tmem_alloc(tmem_holder, TMEM_COLS);
-    tc::tmem_relinquish();
-  }
   // rows of the tiles above the group's realified rows stay zero
   if constexpr (NG * M2 < 128) {
     constexpr int FREE = (128 - NG * M2) * 8;
@@ -141,10 +188,7 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
           make_uint4(0, 0, 0, 0);
     }
   }
-  tc::fence_before_sync();
   __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t taddr = *tmem_holder;
   int kmax = 0;
   for (int s = 0; s < NG; ++s) kmax = max(kmax, nr_s[s]);
   const int nchunks = (kmax + KC - 1) / KC;
@@ -158,11 +202,12 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
   // ---- Gram mainloop --------------------------------------------------------
   const uint32_t idesc = tc::idesc_f16(128, 128, BF16);
   const uint32_t tiles_u32 = smem_u32(tiles);
+  uint64_t *bar_mma = bar_tma + 1;
   bool ok = true;
   for (int c = 0; c < nchunks && ok; ++c) {
     const int buf = c & 1;
     // the MMAs of chunk c - 2 read this tile
-    if (c >= 2) ok = mbar_wait_cta(bar_mma + buf, ((c >> 1) - 1) & 1);
+    if (c >= 2) ok = tc_wait_mma(cx, buf);
     if (!ok) break;
     // item = (antenna octet g8, system s, user u): eight coalesced 8-byte
     // loads, Re into tile row s*2UP + u, Im into row s*2UP + UP + u
@@ -199,24 +244,14 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
       }
       tc::commit(bar_mma + buf);
     }
+    ++cx.mma_commits[buf];
   }
-  if (ok && nchunks > 0) {
-    const int last = nchunks - 1;
-    ok = mbar_wait_cta(bar_mma + (last & 1), (last >> 1) & 1);
-  }
+  // drain: wait for every outstanding commit (the last one covers all MMAs)
+  for (int b = 0; b < 2 && ok; ++b)
+    while (ok && cx.mma_waits[b] < cx.mma_commits[b]) ok = tc_wait_mma(cx, b);
   tc::fence_after_sync();
 
-  if (!ok) {  // let anything in flight land, free TMEM, report
-    if (tid == 0) {
-      mbar_wait(bar_mma, 0);
-      mbar_wait(bar_mma + 1, 0);
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) {
-      tc::fence_after_sync();
-      tc::tmem_dealloc(taddr, TMEM_COLS);
-    }
+  if (!ok) {  // report; the caller stops and frees TMEM
     for (int s = 0; s < nact; ++s) {
       zero_rows<UP>(nr_s[s], K, X + (size_t)n_s[s] * K * d.B, d.B, lo_s[s], tid);
       if (tid == 0) {
@@ -224,7 +259,7 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
         if (scale_out) scale_out[sys0 + s] = 0.f;
       }
     }
-    return;
+    return false;
   }
 
   // ---- TMEM -> P (the diagonal 2UP x 2UP blocks) ------------------------------
@@ -244,10 +279,7 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) {
-    tc::fence_after_sync();
-    tc::tmem_dealloc(taddr, TMEM_COLS);
-  }
+  tc::fence_after_sync();
 
   // ---- P -> G (Hermitian, lower triangle mirrored) ------------------------------
   for (int e = tid; e < NG * UP * UP; e += NT) {
@@ -317,12 +349,14 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
                         bar_tma);
         }
       }
-      ok = mbar_wait_cta(bar_tma, c & 1);
+      ok = mbar_wait_cta(bar_tma, cx.tma_waits & 1);
       if (!ok) {
-        if (tid == 0) mbar_wait(bar_tma, c & 1);
+        if (tid == 0) mbar_wait(bar_tma, cx.tma_waits & 1);
         __syncthreads();
+        ++cx.tma_waits;
         break;
       }
+      ++cx.tma_waits;
     } else {
       for (int s = 0; s < NG; ++s) {
         const int m = min(KA, nr_s[s] - c * KA);
@@ -369,6 +403,41 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
     status[sys0 + tid] = st_s[tid];
     if (scale_out) scale_out[sys0 + tid] = st_s[tid] == ST_OK ? sc_s[tid] : 0.f;
   }
+  return ok;
+}
+
+
+template <int UP, bool BF16>
+__global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
+    k_fused_tc(InstDesc in, int Kmax) {
+  extern __shared__ unsigned char smem_raw[];
+  TcCtx cx;
+  tc_setup<UP>(cx, smem_raw, Kmax);
+  const int total = in.d.n_sc * in.d.nsys;
+  const int sys0 = blockIdx.x * TcGeo<UP>::NG;
+  tc_group<UP, BF16>(cx, in, sys0, min(TcGeo<UP>::NG, total - sys0));
+  tc_teardown(cx);
+}
+
+// Persistent form: CTAs pull work items (groups of systems of any instance of
+// this bucket) from an atomic queue until it is empty.
+template <int UP, bool BF16>
+__global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
+    k_batch_tc(const InstDesc *__restrict__ insts, const WorkItem *__restrict__ items,
+               int n_items, int *__restrict__ queue, int Kmax) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int next;
+  TcCtx cx;
+  tc_setup<UP>(cx, smem_raw, Kmax);
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(queue, 1);
+    __syncthreads();
+    const int it = next;
+    if (it >= n_items) break;
+    const WorkItem w = items[it];
+    if (!tc_group<UP, BF16>(cx, insts[w.inst], w.sys0, w.nact)) break;
+  }
+  tc_teardown(cx);
 }
 
 template <int UP, bool BF16>
@@ -380,7 +449,19 @@ cudaError_t launch_tc_t(const SysDesc &d, const float2 *H, const float2 *S, floa
   if (e != cudaSuccess) return e;
   const int total = d.n_sc * d.nsys;
   const int grid = (total + TcGeo<UP>::NG - 1) / TcGeo<UP>::NG;
-  k_fused_tc<UP, BF16><<<grid, NT, L.total, s>>>(d, H, S, X, status, scale_out);
+  InstDesc in{d, H, S, X, status, scale_out};
+  k_fused_tc<UP, BF16><<<grid, NT, L.total, s>>>(in, d.K);
+  return cudaGetLastError();
+}
+
+template <int UP, bool BF16>
+cudaError_t launch_batch_tc_t(const InstDesc *insts, const WorkItem *items, int n_items,
+                              int *queue, int Kmax, int grid, cudaStream_t s) {
+  const TcSmem L = tc_smem_layout<UP>(Kmax);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_tc<UP, BF16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e != cudaSuccess) return e;
+  k_batch_tc<UP, BF16><<<grid, NT, L.total, s>>>(insts, items, n_items, queue, Kmax);
   return cudaGetLastError();
 }
 
@@ -394,6 +475,52 @@ cudaError_t launch_tc_u(const SysDesc &d, bool bf16, const float2 *H, const floa
 }  // namespace
 
 bool tc_supported(int UP) { return UP <= 32; }
+
+int tc_systems_per_group(int UP) { return UP > 0 && UP <= 64 ? (128 / (2 * UP) > 0 ? 128 / (2 * UP) : 1) : 1; }
+
+cudaError_t launch_batch_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
+                            int n_items, int *queue, int Kmax, int grid, cudaStream_t s) {
+#define DP_BTC(UPV)                                                                       \
+  case UPV:                                                                               \
+    return bf16 ? launch_batch_tc_t<UPV, true>(insts, items, n_items, queue, Kmax, grid, s) \
+                : launch_batch_tc_t<UPV, false>(insts, items, n_items, queue, Kmax, grid, s);
+  switch (UP) {
+    DP_BTC(8)
+    DP_BTC(16)
+    DP_BTC(24)
+    DP_BTC(32)
+    default: return cudaErrorInvalidValue;
+  }
+#undef DP_BTC
+}
+
+int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax) {
+  int n = 0;
+  size_t bytes = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+#define DP_OCC(UPV)                                                                           \
+  case UPV:                                                                                   \
+    bytes = tc_smem_layout<UPV>(Kmax).total;                                                  \
+    if (bf16) {                                                                               \
+      cudaFuncSetAttribute(k_batch_tc<UPV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                           (int)bytes);                                                       \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_tc<UPV, true>, NT, bytes);  \
+    } else {                                                                                  \
+      cudaFuncSetAttribute(k_batch_tc<UPV, false>,                                            \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);          \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_tc<UPV, false>, NT, bytes); \
+    }                                                                                         \
+    break;
+  switch (UP) {
+    DP_OCC(8)
+    DP_OCC(16)
+    DP_OCC(24)
+    DP_OCC(32)
+    default: break;
+  }
+#undef DP_OCC
+  return e == cudaSuccess ? n : 0;
+}
 
 cudaError_t launch_fused_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
                             float2 *X, int *status, float *scale_out, cudaStream_t s) {

@@ -72,6 +72,16 @@ def load(build_if_missing: bool = True):
         L.dp_status_string.argtypes = [I]
         L.dp_status_string.restype = ctypes.c_char_p
         L.dp_version.restype = ctypes.c_char_p
+        L.dp_batch_create.argtypes = [ctypes.POINTER(PlanDesc), I, P, ctypes.POINTER(P)]
+        L.dp_batch_destroy.argtypes = [P]
+        L.dp_batch_precode.argtypes = [P, P, P, P]
+        L.dp_batch_tune.argtypes = [P, P, P, P, I]
+        L.dp_batch_status_get.argtypes = [P, P]
+        L.dp_batch_describe.argtypes = [P]
+        L.dp_batch_describe.restype = ctypes.c_char_p
+        for name in ("dp_batch_create", "dp_batch_destroy", "dp_batch_precode", "dp_batch_tune",
+                     "dp_batch_status_get"):
+            getattr(L, name).restype = I
         for name in ("dp_plan_create", "dp_plan_destroy", "dp_plan_set_stream", "dp_gram_local",
                      "dp_gram_reduce", "dp_solve", "dp_precode_apply", "dp_precode",
                      "dp_status_get"):
@@ -217,3 +227,84 @@ class Plan:
         import torch
         dt = torch.float32 if name == "scale" else torch.complex64
         return torch.empty(self.shapes()[name], dtype=dt, device="cuda")
+
+
+class Batch:
+    """Batched uneven precoding (dp_batch_t): n instances, each described by a
+    dict with the Plan keyword arguments (U, B, C, n_sc, K, mode, prec, rho2,
+    N0, Es, tau, cluster_sizes).  precode() takes per-instance lists of device
+    tensors in the single-plan layouts."""
+
+    def __init__(self, descs, stream=None):
+        import torch
+        self._lib = load()
+        self.descs = [dict(d) for d in descs]
+        n = len(self.descs)
+        arr = (PlanDesc * n)()
+        self._keep = []
+        for i, d in enumerate(self.descs):
+            cs = d.get("cluster_sizes")
+            ptr = None
+            if cs is not None:
+                c = (ctypes.c_int * len(cs))(*[int(x) for x in cs])
+                self._keep.append(c)
+                ptr = ctypes.cast(c, ctypes.POINTER(ctypes.c_int))
+            arr[i] = PlanDesc(int(d["U"]), int(d["B"]), int(d["C"]), ptr, int(d["n_sc"]),
+                              int(d["K"]), MODES[d.get("mode", "wf")],
+                              PRECISIONS[d.get("prec", "fp32")], float(d.get("rho2", 1.0)),
+                              float(d.get("N0", 0.1)), float(d.get("Es", 1.0)),
+                              float(d.get("tau", 0.125)), 0)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(self._lib.dp_batch_create(arr, n, ctypes.c_void_p(stream.cuda_stream),
+                                         ctypes.byref(h)), "dp_batch_create")
+        self._h = h
+
+    def __len__(self):
+        return len(self.descs)
+
+    def _ptrs(self, tensors):
+        n = len(self.descs)
+        if len(tensors) != n:
+            raise ValueError(f"expected {n} tensors")
+        arr = (ctypes.c_void_p * n)()
+        for i, t in enumerate(tensors):
+            if not (t.is_cuda and t.is_contiguous()):
+                raise ValueError("batch arrays must be contiguous CUDA tensors")
+            arr[i] = t.data_ptr()
+        return arr
+
+    def precode(self, Hs, Ss, Xs):
+        _check(self._lib.dp_batch_precode(self._h, self._ptrs(Hs), self._ptrs(Ss),
+                                          self._ptrs(Xs)), "dp_batch_precode")
+
+    def tune(self, Hs, Ss, Xs, trials: int = 3):
+        _check(self._lib.dp_batch_tune(self._h, self._ptrs(Hs), self._ptrs(Ss), self._ptrs(Xs),
+                                       int(trials)), "dp_batch_tune")
+
+    def status_get(self):
+        total = sum(int(d["n_sc"]) for d in self.descs)
+        out = np.zeros(max(total, 1), np.int32)
+        self._lib.dp_batch_status_get(self._h, out.ctypes.data_as(ctypes.c_void_p))
+        res, o = [], 0
+        for d in self.descs:
+            res.append(out[o:o + int(d["n_sc"])].copy())
+            o += int(d["n_sc"])
+        return res
+
+    def describe(self) -> dict:
+        import json
+        return json.loads(self._lib.dp_batch_describe(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
