@@ -182,6 +182,70 @@ dp_status dp_batch_tune(dp_batch_t b, const void *const *H, const void *const *S
 dp_status dp_batch_status_get(dp_batch_t b, int *host_status);
 const char *dp_batch_describe(dp_batch_t b);
 
+/* ---- Continuous-batching server -------------------------------------------
+ * Serving form of the precoder: a cell is one channel (its dp_plan_desc with
+ * n_sc = subcarriers of one slot, and a device-resident H [n_sc][B][U] owned
+ * by the caller, which may point the cell at a new estimate at any time);
+ * a request precodes one slot of a cell from device symbols S [n_sc][K][U]
+ * into an output X [n_sc][K][B] that the server places in its device arena.
+ * A worker thread admits pending requests in arrival order whenever fewer
+ * than max_inflight are on the GPU and the arena has room for the request's
+ * output and status (admission by free device memory), launches them on the
+ * cell's stream (cells are spread over the streams: requests of different
+ * cells overlap on the GPU, the slots of one cell stay in order) and retires
+ * them when they complete, recording the latency from submission to the
+ * observed completion.  Every request runs the same kernels as dp_precode
+ * with the cell's precision, so its result does not depend on the mix.
+ * The paper has no serving layer; this packages its per-slot precoder
+ * (Sec. IV) for an arrival process of slots. */
+typedef struct {
+  int device;          /* CUDA device the server runs on */
+  int streams;         /* CUDA streams the cells are spread over, 1..64 */
+  int max_inflight;    /* requests on the GPU at once, 1..1024 */
+  size_t arena_bytes;  /* device memory for request outputs and status */
+  int auto_release;    /* 1: a request's output is freed as soon as it completes */
+} dp_server_config;
+
+typedef struct {
+  long long completed, failed, subcarriers;
+  double p50_ms, p99_ms, mean_ms, max_ms;  /* submission -> completion latency */
+  double wall_s;                           /* first submission -> last completion */
+  int inflight_peak;
+  long long arena_high_water;              /* bytes */
+} dp_server_stats_t;
+
+typedef struct dp_server *dp_server_t;
+/* Create the server (allocates its arena and streams, starts its worker). */
+dp_status dp_server_create(const dp_server_config *cfg, dp_server_t *out);
+/* Stop the worker after the submitted requests complete; free everything. */
+dp_status dp_server_destroy(dp_server_t s);
+/* Register a cell (validated like dp_plan_create; K >= 1, n_sc >= 1); H is a
+ * 16-byte aligned device array that must stay valid while the cell uses it.
+ * DP_ERR_OOM if one request of the cell could never fit the arena. */
+dp_status dp_server_add_cell(dp_server_t s, const dp_plan_desc *desc, const void *H, int *cell_id);
+/* Point the cell at another device channel array (requests submitted from
+ * now on use it). */
+dp_status dp_server_set_channel(dp_server_t s, int cell, const void *H);
+/* Submit one slot: S is a device array; returns at once with the id. */
+dp_status dp_server_submit(dp_server_t s, int cell, const void *S, unsigned long long *req_id);
+/* Block until every submitted request has completed. */
+dp_status dp_server_drain(dp_server_t s);
+/* A completed request's output (device pointer into the arena, valid until
+ * released) and its worst per-subcarrier status. */
+dp_status dp_server_result(dp_server_t s, unsigned long long req_id, void **X, int *status);
+/* Copy a completed request's output to dst (device, or host if to_host). */
+dp_status dp_server_copy_result(dp_server_t s, unsigned long long req_id, void *dst, int to_host);
+/* Return a completed request's output buffer to the arena. */
+dp_status dp_server_release(dp_server_t s, unsigned long long req_id);
+/* Open-loop load generator: submit request i for cells[i] with symbols S[i]
+ * at arrival_s[i] seconds after the call (busy-waiting on the host clock;
+ * if H_switch is non-NULL and H_switch[i] is non-NULL, the cell is pointed at
+ * that channel first), then drain. */
+dp_status dp_server_replay(dp_server_t s, int n, const int *cells, const void *const *S,
+                           const double *arrival_s, const void *const *H_switch);
+dp_status dp_server_stats(dp_server_t s, dp_server_stats_t *out);
+dp_status dp_server_reset_stats(dp_server_t s);
+
 /* Allocation-free precoding (the paper has no counterpart: this is a
  * deployment variant of dp_precode).  For callers that cannot call
  * cudaMalloc: a baseband runtime whose device memory is carved up once at

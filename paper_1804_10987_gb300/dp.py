@@ -43,6 +43,19 @@ class PlanDesc(ctypes.Structure):
                 ("tau", ctypes.c_float), ("refine", ctypes.c_int)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("streams", ctypes.c_int), ("max_inflight", ctypes.c_int),
+                ("arena_bytes", ctypes.c_size_t), ("auto_release", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("subcarriers", ctypes.c_longlong), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("inflight_peak", ctypes.c_int), ("arena_high_water", ctypes.c_longlong)]
+
+
 def lib_path() -> str:
     return _build.LIB_PATH
 
@@ -81,6 +94,24 @@ def load(build_if_missing: bool = True):
         L.dp_batch_describe.restype = ctypes.c_char_p
         for name in ("dp_batch_create", "dp_batch_destroy", "dp_batch_precode", "dp_batch_tune",
                      "dp_batch_status_get"):
+            getattr(L, name).restype = I
+        U64 = ctypes.c_ulonglong
+        L.dp_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
+        L.dp_server_destroy.argtypes = [P]
+        L.dp_server_add_cell.argtypes = [P, ctypes.POINTER(PlanDesc), P, ctypes.POINTER(I)]
+        L.dp_server_set_channel.argtypes = [P, I, P]
+        L.dp_server_submit.argtypes = [P, I, P, ctypes.POINTER(U64)]
+        L.dp_server_drain.argtypes = [P]
+        L.dp_server_result.argtypes = [P, U64, ctypes.POINTER(P), ctypes.POINTER(I)]
+        L.dp_server_copy_result.argtypes = [P, U64, P, I]
+        L.dp_server_release.argtypes = [P, U64]
+        L.dp_server_replay.argtypes = [P, I, P, P, P, P]
+        L.dp_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+        L.dp_server_reset_stats.argtypes = [P]
+        for name in ("dp_server_create", "dp_server_destroy", "dp_server_add_cell",
+                     "dp_server_set_channel", "dp_server_submit", "dp_server_drain",
+                     "dp_server_result", "dp_server_copy_result", "dp_server_release",
+                     "dp_server_replay", "dp_server_stats", "dp_server_reset_stats"):
             getattr(L, name).restype = I
         for name in ("dp_plan_create", "dp_plan_destroy", "dp_plan_set_stream", "dp_gram_local",
                      "dp_gram_reduce", "dp_solve", "dp_precode_apply", "dp_precode",
@@ -301,6 +332,106 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.dp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _desc(d: dict):
+    keep = None
+    ptr = None
+    cs = d.get("cluster_sizes")
+    if cs is not None:
+        keep = (ctypes.c_int * len(cs))(*[int(x) for x in cs])
+        ptr = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
+    pd = PlanDesc(int(d["U"]), int(d["B"]), int(d["C"]), ptr, int(d["n_sc"]), int(d["K"]),
+                  MODES[d.get("mode", "wf")], PRECISIONS[d.get("prec", "fp32")],
+                  float(d.get("rho2", 1.0)), float(d.get("N0", 0.1)), float(d.get("Es", 1.0)),
+                  float(d.get("tau", 0.125)), 0)
+    return pd, keep
+
+
+class Server:
+    """Continuous-batching server (dp_server_t).  Cells hold device-resident
+    channels; requests precode one slot from device symbols into the
+    server's arena."""
+
+    def __init__(self, streams: int = 8, max_inflight: int = 32, arena_bytes: int = 1 << 30,
+                 auto_release: bool = False, device: int = 0):
+        self._lib = load()
+        cfg = ServerConfig(int(device), int(streams), int(max_inflight), int(arena_bytes),
+                           int(bool(auto_release)))
+        h = ctypes.c_void_p()
+        _check(self._lib.dp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "dp_server_create")
+        self._h = h
+        self.cells = []
+        self._hold = []
+
+    def add_cell(self, desc: dict, H) -> int:
+        pd, keep = _desc(desc)
+        cid = ctypes.c_int()
+        _check(self._lib.dp_server_add_cell(self._h, ctypes.byref(pd), ctypes.c_void_p(H.data_ptr()),
+                                            ctypes.byref(cid)), "dp_server_add_cell")
+        self.cells.append(dict(desc))
+        self._hold.append(H)
+        return cid.value
+
+    def set_channel(self, cell: int, H):
+        self._hold.append(H)
+        _check(self._lib.dp_server_set_channel(self._h, int(cell), ctypes.c_void_p(H.data_ptr())),
+               "dp_server_set_channel")
+
+    def submit(self, cell: int, S) -> int:
+        rid = ctypes.c_ulonglong()
+        _check(self._lib.dp_server_submit(self._h, int(cell), ctypes.c_void_p(S.data_ptr()),
+                                          ctypes.byref(rid)), "dp_server_submit")
+        return rid.value
+
+    def drain(self):
+        _check(self._lib.dp_server_drain(self._h), "dp_server_drain")
+
+    def result(self, rid: int):
+        """(X as a new torch tensor copied out of the arena, worst status)."""
+        import torch
+        x = ctypes.c_void_p()
+        st = ctypes.c_int()
+        _check(self._lib.dp_server_result(self._h, ctypes.c_ulonglong(rid), ctypes.byref(x),
+                                          ctypes.byref(st)), "dp_server_result")
+        return st.value
+
+    def copy_result(self, rid: int, out):
+        _check(self._lib.dp_server_copy_result(self._h, ctypes.c_ulonglong(rid),
+                                               ctypes.c_void_p(out.data_ptr()), int(not out.is_cuda)),
+               "dp_server_copy_result")
+
+    def release(self, rid: int):
+        _check(self._lib.dp_server_release(self._h, ctypes.c_ulonglong(rid)), "dp_server_release")
+
+    def replay(self, cells, S_list, arrival_s, H_switch=None):
+        n = len(cells)
+        c = (ctypes.c_int * n)(*[int(x) for x in cells])
+        sp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in S_list])
+        at = (ctypes.c_double * n)(*[float(t) for t in arrival_s])
+        hs = None
+        if H_switch is not None:
+            hs = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in H_switch])
+        _check(self._lib.dp_server_replay(self._h, n, c, sp, at, hs), "dp_server_replay")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(self._lib.dp_server_stats(self._h, ctypes.byref(s)), "dp_server_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(self._lib.dp_server_reset_stats(self._h), "dp_server_reset_stats")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.dp_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
