@@ -21,6 +21,9 @@ struct dp_plan {
   int *d_off = nullptr;     // [C + 1]
   int *d_status = nullptr;  // [n_sc * nsys]: status of every system of the last call
   int nsys = 1;
+  // FD-WF clusters with B_c < U (<= 32) run the B_c x B_c form
+  bool has_small = false, all_small = false;
+  int bcp = 0;
   // workspace of the streaming (unfused) form of dp_precode
   float2 *w_G = nullptr;
   float2 *w_Z = nullptr;
@@ -167,6 +170,17 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
   p->UP = dp::padded_users(d.U);
   p->maxrows_sys = (d.mode == DP_FDWF) ? maxbc : d.B;
   p->nsys = (d.mode == DP_FDWF) ? d.C : 1;
+  if (d.mode == DP_FDWF) {
+    int maxsmall = 0, nsmall = 0;
+    for (int c = 0; c < d.C; ++c)
+      if (sizes[c] < d.U && sizes[c] <= 32) {
+        ++nsmall;
+        maxsmall = sizes[c] > maxsmall ? sizes[c] : maxsmall;
+      }
+    p->has_small = nsmall > 0;
+    p->all_small = nsmall == d.C;
+    p->bcp = dp::fd_small_bcp(maxsmall);
+  }
   p->fused_fits = dp::fused_smem_bytes(p->UP, p->maxrows_sys, d.K) != 0;
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     cudaGetLastError();
@@ -271,7 +285,12 @@ dp_status dp_precode(dp_plan_t p, const void *H, const void *S, void *X) {
   const float2 *h = static_cast<const float2 *>(H);
   const float2 *sy = static_cast<const float2 *>(S);
   float2 *x = static_cast<float2 *>(X);
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
+  if (p->has_small) {  // FD-WF clusters with B_c < U: the paper's B_c x B_c form
+    sd.skip_small = 1;
+    e = dp::launch_fd_small(dp::InstDesc{sd, h, sy, x, p->d_status, nullptr}, p->bcp, p->stream);
+    if (e != cudaSuccess || p->all_small) return cuda_status(e);
+  }
   if (p->d.prec != DP_FP32)
     return cuda_status(dp::launch_fused_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, p->d_status,
                                            nullptr, p->stream));

@@ -26,7 +26,7 @@
 
 namespace {
 
-enum Family { FAM_TC = 0, FAM_FUSED = 1, FAM_STREAM = 2 };
+enum Family { FAM_TC = 0, FAM_FUSED = 1, FAM_STREAM = 2, FAM_FDSMALL = 3 };
 
 struct Bucket {
   int family;
@@ -46,6 +46,8 @@ struct Inst {
   std::vector<int> off;
   int UP, nsys, maxrows, family;
   bool bf16;
+  bool has_small = false, all_small = false;  // FD-WF clusters with B_c < U
+  int bcp = 0;
   size_t status_off;  // offset of this instance's status block in the batch array
   // workspace of the streaming family
   float2 *w_G = nullptr, *w_Z = nullptr;
@@ -109,6 +111,7 @@ dp::SysDesc sys_of(const Inst &in, const void *H) {
     s.rho2_sys = (float)(rho2 / C);
   }
   s.tma_ok = (d.U % 2 == 0) && (H == nullptr || a16(H));
+  s.skip_small = in.has_small ? 1 : 0;
   return s;
 }
 
@@ -159,6 +162,9 @@ cudaError_t enqueue_bucket(dp_batch *b, int k, cudaStream_t s) {
   if (bk.family == FAM_TC)
     return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, (int)bk.items.size(),
                                b->d_queues + k, bk.Kmax, grid, s);
+  if (bk.family == FAM_FDSMALL)
+    return dp::launch_batch_fd_small(bk.UP, b->d_insts, bk.d_items, (int)bk.items.size(),
+                                     b->d_queues + k, bk.Kmax, grid, s);
   return dp::launch_batch_fused(bk.UP, b->d_insts, bk.d_items, (int)bk.items.size(),
                                 b->d_queues + k, bk.maxrows, bk.Kmax, grid, s);
 }
@@ -167,7 +173,12 @@ cudaError_t enqueue_streaming(dp_batch *b, int i, cudaStream_t s) {
   Inst &in = b->insts[i];
   const dp::InstDesc &t = b->h_insts[i];
   if (in.d.n_sc == 0) return cudaSuccess;
-  cudaError_t e = dp::launch_gram(t.d, in.UP, t.H, in.w_G, s);
+  cudaError_t e = cudaSuccess;
+  if (in.has_small) {
+    e = dp::launch_fd_small(t, in.bcp, s);
+    if (e != cudaSuccess || in.all_small) return e;
+  }
+  e = dp::launch_gram(t.d, in.UP, t.H, in.w_G, s);
   if (e == cudaSuccess) e = dp::launch_solve(t.d, in.UP, in.w_G, t.S, in.w_Z, in.w_scale, t.status, s);
   if (e == cudaSuccess && in.d.K > 0) e = dp::launch_apply(t.d, in.UP, t.H, in.w_Z, in.w_scale, t.X, s);
   return e;
@@ -252,7 +263,8 @@ void describe(dp_batch *b) {
                   "%s{\"family\": \"%s\", \"users_padded\": %d, \"items\": %zu, "
                   "\"ctas_per_sm\": %d, \"max_ctas_per_sm\": %d, \"tuned_ms\": %.4f}",
                   k ? ", " : "",
-                  bk.family == FAM_TC ? (bk.bf16 ? "tc_bf16" : "tc_fp16") : "fp32_fused", bk.UP,
+                  bk.family == FAM_TC ? (bk.bf16 ? "tc_bf16" : "tc_fp16")
+                  : bk.family == FAM_FDSMALL ? "fd_small_clusters" : "fp32_fused", bk.UP,
                   bk.items.size(), bk.blocks, bk.max_blocks, bk.tuned_ms);
     s += buf;
   }
@@ -291,6 +303,19 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
     for (int c = 0; c < in.d.C; ++c) maxbc = std::max(maxbc, in.off[c + 1] - in.off[c]);
     in.maxrows = in.d.mode == DP_FDWF ? maxbc : in.d.B;
     in.bf16 = in.d.prec == DP_BF16;
+    if (in.d.mode == DP_FDWF) {
+      int maxsmall = 0, nsmall = 0;
+      for (int c = 0; c < in.d.C; ++c) {
+        const int bc = in.off[c + 1] - in.off[c];
+        if (bc < in.d.U && bc <= 32) {
+          ++nsmall;
+          maxsmall = std::max(maxsmall, bc);
+        }
+      }
+      in.has_small = nsmall > 0;
+      in.all_small = nsmall == in.d.C;
+      in.bcp = dp::fd_small_bcp(maxsmall);
+    }
     if (in.d.prec != DP_FP32 && dp::tc_supported(in.UP)) in.family = FAM_TC;
     else if (dp::fused_smem_bytes(in.UP, in.maxrows, in.d.K) != 0) in.family = FAM_FUSED;
     else in.family = FAM_STREAM;
@@ -315,6 +340,31 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
     cudaMemcpy(in.d_off, in.off.data(), sizeof(int) * in.off.size(), cudaMemcpyHostToDevice);
     const int nsys_total = in.d.n_sc * in.nsys;
     if (nsys_total == 0) continue;
+    if (in.has_small && in.family != FAM_STREAM) {
+      // small clusters: one item per system in the B_c x B_c bucket
+      auto key = std::make_tuple((int)FAM_FDSMALL, in.bcp, 0);
+      auto it = bucket_of.find(key);
+      int k;
+      if (it == bucket_of.end()) {
+        k = (int)b->buckets.size();
+        bucket_of[key] = k;
+        Bucket bk;
+        bk.family = FAM_FDSMALL;
+        bk.UP = in.bcp;
+        bk.bf16 = false;
+        b->buckets.push_back(bk);
+      } else {
+        k = it->second;
+      }
+      Bucket &bk = b->buckets[k];
+      bk.Kmax = std::max(bk.Kmax, in.d.K);
+      for (int n = 0; n < in.d.n_sc; ++n)
+        for (int c = 0; c < in.d.C; ++c) {
+          const int bc = in.off[c + 1] - in.off[c];
+          if (bc < in.d.U && bc <= 32) bk.items.push_back(dp::WorkItem{i, n * in.nsys + c, 1});
+        }
+      if (in.all_small) continue;
+    }
     if (in.family == FAM_STREAM) {
       b->streaming.push_back(i);
       oom = cudaMalloc(&in.w_G, sizeof(float2) * nsys_total * in.d.U * in.d.U) != cudaSuccess ||
@@ -353,7 +403,7 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
   for (auto &bk : b->buckets) {
     auto cost = [&](const dp::WorkItem &w) {
       const Inst &in = b->insts[w.inst];
-      return (long long)in.maxrows * in.UP * w.nact;
+      return (long long)in.maxrows * in.UP * in.UP * w.nact;
     };
     std::stable_sort(bk.items.begin(), bk.items.end(),
                      [&](const dp::WorkItem &a, const dp::WorkItem &c) { return cost(a) > cost(c); });
@@ -363,8 +413,11 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
     }
     cudaMemcpy(bk.d_items, bk.items.data(), sizeof(dp::WorkItem) * bk.items.size(),
                cudaMemcpyHostToDevice);
-    bk.max_blocks = bk.family == FAM_TC ? dp::tc_max_blocks_per_sm(bk.UP, bk.bf16, bk.Kmax)
-                                        : dp::fused_max_blocks_per_sm(bk.UP, bk.maxrows, bk.Kmax);
+    bk.max_blocks = bk.family == FAM_TC
+                        ? dp::tc_max_blocks_per_sm(bk.UP, bk.bf16, bk.Kmax)
+                        : bk.family == FAM_FDSMALL
+                              ? dp::fd_small_max_blocks_per_sm(bk.UP, bk.Kmax)
+                              : dp::fused_max_blocks_per_sm(bk.UP, bk.maxrows, bk.Kmax);
     if (bk.max_blocks < 1) {
       free_batch(b);
       return DP_ERR_UNSUPPORTED;

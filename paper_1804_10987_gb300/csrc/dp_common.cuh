@@ -136,6 +136,8 @@ struct SysDesc {
   float rho2_sys;   // power of one system: rho^2, or rho^2 / C in FD-WF
   float Es;
   int tma_ok;       // rows may be fetched with 1-D bulk copies
+  int skip_small;   // FD-WF: systems with fewer antennas than users (and at
+                    // most 32) are left to the B_c x B_c kernel
 };
 
 // One precoding instance: its systems and its device arrays (H [n_sc][B][U],
@@ -156,6 +158,11 @@ struct WorkItem {
   int sys0;
   int nact;
 };
+
+// True for a system the B_c x B_c small-cluster kernel handles instead.
+__device__ __forceinline__ bool sys_is_small(const SysDesc &d, int nrows) {
+  return d.skip_small && d.nsys > 1 && nrows < d.U && nrows <= 32;
+}
 
 __device__ __forceinline__ void sys_rows(const SysDesc &d, int g, int &lo, int &hi) {
   if (d.nsys == 1) {

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(NT) k_gram(SysDesc d, const float2 *__restrict
   int lo, hi;
   sys_rows(d, g, lo, hi);
   const int nrows = hi - lo;
+  if (sys_is_small(d, nrows)) return;
   float *Hs = reinterpret_cast<float *>(smem_raw);
   float2 *G = reinterpret_cast<float2 *>(Hs + (size_t)chunk * RS);
   uint64_t *bar = reinterpret_cast<uint64_t *>(G + UP * UP);
@@ -108,6 +109,11 @@ __global__ void __launch_bounds__(NT) k_solve_warp(SysDesc d, const float2 *__re
   if (sys >= nsys_total) return;  // warp-uniform; no CTA barriers below
   const int n = sys / d.nsys, g = sys - n * d.nsys;
   const int U = d.U, K = d.K;
+  {
+    int lo, hi;
+    sys_rows(d, g, lo, hi);
+    if (sys_is_small(d, hi - lo)) return;
+  }
   float2 *Gw = reinterpret_cast<float2 *>(smem_raw) + (size_t)w * (UP * UP + K * UP);
   float2 *Sw = Gw + UP * UP;
 
@@ -156,6 +162,11 @@ __global__ void __launch_bounds__(NT) k_solve_cta(SysDesc d, const float2 *__res
   const int sys = blockIdx.x;
   const int n = sys / d.nsys, g = sys - n * d.nsys;
   const int U = d.U, K = d.K;
+  {
+    int lo, hi;
+    sys_rows(d, g, lo, hi);
+    if (sys_is_small(d, hi - lo)) return;
+  }
   float2 *G = reinterpret_cast<float2 *>(smem_raw);
   float2 *A = G + UP * UP;
   float2 *Ss = A + UP * UP;
@@ -212,6 +223,7 @@ __global__ void __launch_bounds__(NT) k_apply(SysDesc d, const float2 *__restric
   int lo, hi;
   sys_rows(d, g, lo, hi);
   const int nrows = hi - lo;
+  if (sys_is_small(d, nrows)) return;
   const int U = d.U, K = d.K;
   float *Hs = reinterpret_cast<float *>(smem_raw);
   float2 *Zs = reinterpret_cast<float2 *>(Hs + (size_t)chunk * RS);
@@ -281,6 +293,7 @@ __device__ bool fused_system(const InstDesc &in, int sys, unsigned char *smem_ra
   int lo, hi;
   sys_rows(d, g, lo, hi);
   const int nrows = hi - lo;
+  if (sys_is_small(d, nrows)) return true;  // the B_c x B_c kernel's system
   const int U = d.U, K = d.K;
   float *Hs = reinterpret_cast<float *>(smem_raw);
   float2 *G = reinterpret_cast<float2 *>(Hs + (size_t)maxrows * RS);
@@ -392,9 +405,13 @@ __global__ void __launch_bounds__(NT) k_batch_fused(const InstDesc *__restrict__
   }
 }
 
+// Allow `bytes` of dynamic shared memory and ask for the largest shared
+// carve-out, so that the SM is configured for as many CTAs as fit.
 template <typename KernelT>
 cudaError_t set_smem(KernelT k, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess || bytes <= 48 * 1024) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 

@@ -44,4 +44,12 @@ cudaError_t launch_batch_tc(int UP, bool bf16, const InstDesc *insts, const Work
                             int n_items, int *queue, int Kmax, int grid, cudaStream_t s);
 int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax);
 
+// FD-WF clusters with B_c < U (and B_c <= 32) in the B_c x B_c form:
+// padded cluster width (8, 16, 32; 0 if none fits) and the launchers.
+int fd_small_bcp(int maxbc);
+cudaError_t launch_fd_small(const InstDesc &in, int bcp, cudaStream_t s);
+cudaError_t launch_batch_fd_small(int bcp, const InstDesc *insts, const WorkItem *items,
+                                  int n_items, int *queue, int Kmax, int grid, cudaStream_t s);
+int fd_small_max_blocks_per_sm(int bcp, int Kmax);
+
 }  // namespace dp

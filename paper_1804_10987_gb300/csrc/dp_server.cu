@@ -95,6 +95,8 @@ struct Cell {
   int *d_off = nullptr;
   int UP = 8, nsys = 1, maxrows = 0;
   bool tc = false, fused = false;
+  bool has_small = false, all_small = false;  // FD-WF clusters with B_c < U
+  int bcp = 0;
   const void *H = nullptr;
   int stream = 0;
   size_t x_bytes = 0, st_bytes = 0;
@@ -166,6 +168,7 @@ dp::SysDesc sys_of(const Cell &c, const void *H) {
     s.rho2_sys = (float)(rho2 / C);
   }
   s.tma_ok = (d.U % 2 == 0) && a16(H);
+  s.skip_small = c.has_small ? 1 : 0;
   return s;
 }
 
@@ -177,8 +180,10 @@ cudaError_t launch_request(dp_server *sv, Request *r) {
   const float2 *S = static_cast<const float2 *>(r->S);
   float2 *X = reinterpret_cast<float2 *>(sv->arena.ptr(r->x_off));
   int *status = reinterpret_cast<int *>(sv->arena.ptr(r->st_off));
-  cudaError_t e;
-  if (c.tc)
+  cudaError_t e = cudaSuccess;
+  if (c.has_small) e = dp::launch_fd_small(dp::InstDesc{d, H, S, X, status, nullptr}, c.bcp, st);
+  if (e != cudaSuccess || c.all_small) {
+  } else if (c.tc)
     e = dp::launch_fused_tc(d, c.UP, c.d.prec == DP_BF16, H, S, X, status, nullptr, st);
   else if (c.fused)
     e = dp::launch_fused(d, c.UP, c.maxrows, H, S, X, status, nullptr, st);
@@ -360,6 +365,19 @@ dp_status dp_server_add_cell(dp_server_t sv, const dp_plan_desc *desc, const voi
   c.UP = dp::padded_users(d.U);
   c.nsys = d.mode == DP_FDWF ? d.C : 1;
   c.maxrows = d.mode == DP_FDWF ? maxbc : d.B;
+  if (d.mode == DP_FDWF) {
+    int maxsmall = 0, nsmall = 0;
+    for (int k = 0; k < d.C; ++k) {
+      const int bc = c.off[k + 1] - c.off[k];
+      if (bc < d.U && bc <= 32) {
+        ++nsmall;
+        maxsmall = std::max(maxsmall, bc);
+      }
+    }
+    c.has_small = nsmall > 0;
+    c.all_small = nsmall == d.C;
+    c.bcp = dp::fd_small_bcp(maxsmall);
+  }
   c.tc = d.prec != DP_FP32 && dp::tc_supported(c.UP);
   c.fused = !c.tc && dp::fused_smem_bytes(c.UP, c.maxrows, d.K) != 0;
   c.H = H;

@@ -70,7 +70,7 @@ __host__ __device__ TcSmem tc_smem_layout(int K) {
   L.Z = take((size_t)T::NG * K * UP * 8 + 16, 16);
   L.scale = take((size_t)T::NG * 4, 16);
   L.status = take((size_t)T::NG * 4, 16);
-  L.info = take((size_t)T::NG * 3 * 4, 16);
+  L.info = take((size_t)T::NG * 4 * 4, 16);
   L.bars = take(3 * 8, 8);
   L.tmem = take(4, 4);
   L.total = o + 1024;  // slack to align the dynamic base to 1024 bytes
@@ -158,6 +158,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   int *lo_s = reinterpret_cast<int *>(base + L.info);  // first antenna of each system
   int *nr_s = lo_s + NG;                                // antennas of each system
   int *n_s = nr_s + NG;                                 // subcarrier of each system
+  int *sk_s = n_s + NG;                                 // system left to another kernel
   uint64_t *bar_tma = reinterpret_cast<uint64_t *>(base + L.bars);
   const uint32_t taddr = cx.taddr;
 
@@ -168,15 +169,18 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   // ---- systems of the group, symbols -----------------------------------------
   __syncthreads();  // the previous group is done with every shared buffer
   if (tid < NG) {
-    int lo = 0, hi = 0, n = 0;
+    int lo = 0, hi = 0, n = 0, skip = 1;
     if (tid < nact) {
       const int sys = sys0 + tid;
       n = sys / d.nsys;
       sys_rows(d, sys - n * d.nsys, lo, hi);
+      skip = sys_is_small(d, hi - lo);  // the B_c x B_c kernel's system
+      if (skip) hi = lo;
     }
     lo_s[tid] = lo;
     nr_s[tid] = hi - lo;
     n_s[tid] = n;
+    sk_s[tid] = skip;
   }
   // rows of the tiles above the group's realified rows stay zero
   if constexpr (NG * M2 < 128) {
@@ -253,6 +257,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
 
   if (!ok) {  // report; the caller stops and frees TMEM
     for (int s = 0; s < nact; ++s) {
+      if (sk_s[s]) continue;
       zero_rows<UP>(nr_s[s], K, X + (size_t)n_s[s] * K * d.B, d.B, lo_s[s], tid);
       if (tid == 0) {
         status[sys0 + s] = ST_TIMEOUT;
@@ -394,12 +399,13 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   }
   if (!ok) {
     for (int s = 0; s < nact; ++s) {
+      if (sk_s[s]) continue;
       zero_rows<UP>(nr_s[s], K, X + (size_t)n_s[s] * K * d.B, d.B, lo_s[s], tid);
       if (tid == 0) st_s[s] = ST_TIMEOUT;
     }
   }
   __syncthreads();
-  if (tid < nact) {
+  if (tid < nact && !sk_s[tid]) {
     status[sys0 + tid] = st_s[tid];
     if (scale_out) scale_out[sys0 + tid] = st_s[tid] == ST_OK ? sc_s[tid] : 0.f;
   }
@@ -446,6 +452,9 @@ cudaError_t launch_tc_t(const SysDesc &d, const float2 *H, const float2 *S, floa
   const TcSmem L = tc_smem_layout<UP>(d.K);
   cudaError_t e = cudaFuncSetAttribute(k_fused_tc<UP, BF16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fused_tc<UP, BF16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   const int total = d.n_sc * d.nsys;
   const int grid = (total + TcGeo<UP>::NG - 1) / TcGeo<UP>::NG;
@@ -460,6 +469,9 @@ cudaError_t launch_batch_tc_t(const InstDesc *insts, const WorkItem *items, int 
   const TcSmem L = tc_smem_layout<UP>(Kmax);
   cudaError_t e = cudaFuncSetAttribute(k_batch_tc<UP, BF16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_tc<UP, BF16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   k_batch_tc<UP, BF16><<<grid, NT, L.total, s>>>(insts, items, n_items, queue, Kmax);
   return cudaGetLastError();
@@ -504,10 +516,16 @@ int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax) {
     if (bf16) {                                                                               \
       cudaFuncSetAttribute(k_batch_tc<UPV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                            (int)bytes);                                                       \
+      cudaFuncSetAttribute(k_batch_tc<UPV, true>,                                             \
+                           cudaFuncAttributePreferredSharedMemoryCarveout,                    \
+                           (int)cudaSharedmemCarveoutMaxShared);                              \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_tc<UPV, true>, NT, bytes);  \
     } else {                                                                                  \
       cudaFuncSetAttribute(k_batch_tc<UPV, false>,                                            \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);          \
+      cudaFuncSetAttribute(k_batch_tc<UPV, false>,                                            \
+                           cudaFuncAttributePreferredSharedMemoryCarveout,                    \
+                           (int)cudaSharedmemCarveoutMaxShared);                              \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_tc<UPV, false>, NT, bytes); \
     }                                                                                         \
     break;

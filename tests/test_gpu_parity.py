@@ -186,3 +186,24 @@ def test_power_normalization_on_gpu():
         pw = np.sum(np.abs(Xg.astype(np.complex128)) ** 2, axis=(1, 2))
         np.testing.assert_allclose(pw, p.rho2, rtol=2e-5)
     _ = torch
+
+
+# --- FD-WF clusters with B_c < U: the paper's B_c x B_c form -----------------------
+
+@pytest.mark.parametrize("U,cs,n_sc,K,snr", [
+    (64, [8] * 32, 20, 14, 10.0),           # all clusters small (B_c = 8 < U = 64)
+    (48, [32] * 8, 9, 14, 0.0),             # B_c = 32 < U = 48, low SNR
+    (16, [2, 30, 5, 64, 1], 11, 7, 20.0),   # mixed: small and U x U clusters
+    (64, [16, 16, 32, 64, 128], 4, 3, 10.0),
+    (33, [32, 32, 1], 6, 14, 5.0),          # B_c = 32 at the kernel's limit, U odd
+])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_fd_small_clusters(U, cs, n_sc, K, snr, prec):
+    p = synth.make_problem(U, sum(cs), len(cs), n_sc, K, 64, snr, seed=3000 + U + len(cs),
+                           mode="fdwf", cluster_sizes=cs)
+    Xg, st = gpu_precode(p, prec=prec if U <= 32 else "fp32")
+    ref = oracle_of(p)  # the oracle takes the B_c x B_c form for B_c < U
+    assert np.array_equal(st, ref["status"])
+    err = rel_err_per_sc(Xg, ref["X"])
+    tol = TOL_FP32 if (prec == "fp32" or U > 32) else 1e-3
+    assert err.max() <= tol, err.max()
