@@ -27,6 +27,7 @@ namespace {
 constexpr int KC = 64;          // antennas per Gram chunk (one 128-byte K-block of 16-bit data)
 constexpr int KA = 64;          // antenna rows per system and apply chunk
 constexpr int TILE_BYTES = 128 * 128;
+constexpr int BOP = 32 * 128;  // bytes of one B operand of the apply (32 rows x 128 B)
 constexpr int TMEM_COLS = 128;
 
 template <int UP>
@@ -34,15 +35,17 @@ struct TcGeo {
   static constexpr int NG = (128 / (2 * UP)) > 0 ? 128 / (2 * UP) : 1;  // systems per CTA
   static constexpr int RS = Geo<UP>::RS;
   static constexpr int M2 = 2 * UP;
-  // one region holds the two tiles, then P, then the apply rows
-  static constexpr int APPLY_BYTES = NG * KA * RS * 4;
-  static constexpr int REGION = APPLY_BYTES > 2 * TILE_BYTES ? APPLY_BYTES : 2 * TILE_BYTES;
+  // one region holds the two Gram tiles, then P, then the apply operands:
+  // A hi / lo tiles (128 antennas x 64 16-bit entries) and three B operands
+  // (32 symbol rows x 64 entries)
+  static constexpr int BOP_BYTES = 32 * 128;
+  static constexpr int REGION = 2 * TILE_BYTES + 3 * BOP_BYTES;
   // P blocks padded by one float, or XOR-swizzled when that does not fit
   static constexpr bool P_PAD = (size_t)NG * M2 * (M2 + 1) * 4 <= REGION;
   static constexpr int PS = P_PAD ? M2 + 1 : M2;
   static_assert(P_PAD || (M2 % 32 == 0), "swizzled P needs 32-float rows");
   static_assert((size_t)NG * M2 * PS * 4 <= REGION, "P fits the region");
-  static_assert((size_t)NG * KA * RS * 4 <= REGION, "apply rows fit the region");
+  static_assert(2 * UP <= 64, "realified users fit one 128-byte K-block");
   static constexpr int MIN_BLOCKS = UP <= 16 ? 2 : 1;
   __device__ static __forceinline__ int p_index(int s, int r, int c) {
     return (s * M2 + r) * PS + (P_PAD ? c : (c ^ (r & 31)));
@@ -68,7 +71,7 @@ __host__ __device__ TcSmem tc_smem_layout(int K) {
   L.G = take((size_t)T::NG * UP * UP * 8, 16);
   L.S = take((size_t)T::NG * K * UP * 8 + 16, 16);
   L.Z = take((size_t)T::NG * K * UP * 8 + 16, 16);
-  L.scale = take((size_t)T::NG * 4, 16);
+  L.scale = take((size_t)(T::NG + NT / 32) * 4, 16);
   L.status = take((size_t)T::NG * 4, 16);
   L.info = take((size_t)T::NG * 4 * 4, 16);
   L.bars = take(3 * 8, 8);
@@ -307,8 +310,6 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
     fin = __all_sync(FULL, fin);
     if (lane == 0) st_s[warp] = fin ? ST_OK : ST_NONFINITE;
   }
-  // the region is free again: zero the pads of the apply rows
-  zero_row_pads<UP>(stage, NG * KA, U, tid);
   __syncthreads();
 
   // ---- solve: one warp per system --------------------------------------------
@@ -325,77 +326,156 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   fence_proxy_async_smem();
   __syncthreads();
 
-  // ---- apply: rows bulk-copied again (L2) into padded rows -------------------
-  const int achunks = (kmax + KA - 1) / KA;
-  const int Kh = (K + 1) / 2;  // two threads per row, each half of the symbols
-  for (int c = 0; c < achunks && ok; ++c) {
-    if (c > 0) {
-      fence_proxy_async_smem();
-      __syncthreads();  // previous rows consumed
+  // ---- apply on the tensor cores --------------------------------------------
+  // Per 128-antenna M-tile: D[b][n] = sum_j A[b][j] Bm[n][j] with A[b][2u + r]
+  // = (Re, Im) H[b][u] and, for symbol q of a chunk of 16, Bm[2q] = (Re z_u,
+  // Im z_u)_u and Bm[2q + 1] = (Im z_u, -Re z_u)_u, so that D[b][2q] + i
+  // D[b][2q + 1] = sum_u conj(H[b][u]) z_q[u].  Split FP16 keeps ~22 bits:
+  // A = A_hi + 2^-11 A_lo, z = z_hi + z_lo, D = A_hi z_hi + A_hi z_lo +
+  // A_lo (2^-11 z_hi); z is first normalized by a power of two per system.
+  {
+    unsigned char *a_hi = base + L.region;
+    unsigned char *a_lo = a_hi + TILE_BYTES;
+    unsigned char *b_op = a_hi + 2 * TILE_BYTES;  // hi, lo, hi * 2^-11
+    const uint32_t a_hi_u = smem_u32(a_hi), a_lo_u = smem_u32(a_lo), b_u = smem_u32(b_op);
+    const uint32_t idesc_ap = tc::idesc_f16(128, 32, false);
+    constexpr int KCH = (2 * UP + 7) / 8;  // 16-byte chunks of a realified row
+    constexpr int KSTEPS = (2 * UP + 15) / 16;
+    // the chunks of the A tiles beyond the realified row stay zero
+    for (int e = tid; e < 2 * 128 * (8 - KCH); e += NT) {
+      const int t = e / (128 * (8 - KCH)), r = e - t * 128 * (8 - KCH);
+      const int m = r / (8 - KCH), c8 = KCH + r % (8 - KCH);
+      *reinterpret_cast<uint4 *>(a_hi + t * TILE_BYTES + tc::sw128_offset(m, c8)) =
+          make_uint4(0, 0, 0, 0);
     }
-    if (tma) {
-      if (warp == 0) {
-        uint32_t bytes = 0;
-        for (int s = 0; s < NG; ++s) {
-          const int m = min(KA, nr_s[s] - c * KA);
-          if (m > 0 && st_s[s] == ST_OK) bytes += (uint32_t)m * U * 8u;
-        }
-        if (lane == 0) {
-          if (bytes) mbar_arrive_expect_tx(bar_tma, bytes);
-          else mbar_arrive(bar_tma);
-        }
-        __syncwarp();
-        for (int s = 0; s < NG; ++s) {
-          const int m = min(KA, nr_s[s] - c * KA);
-          if (m <= 0 || st_s[s] != ST_OK) continue;
-          const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KA) * U;
-          for (int r = lane; r < m; r += 32)
-            tma_load_1d(stage + ((size_t)s * KA + r) * RS, src + (size_t)r * U, (uint32_t)U * 8u,
-                        bar_tma);
-        }
-      }
-      ok = mbar_wait_cta(bar_tma, cx.tma_waits & 1);
-      if (!ok) {
-        if (tid == 0) mbar_wait(bar_tma, cx.tma_waits & 1);
-        __syncthreads();
-        ++cx.tma_waits;
-        break;
-      }
-      ++cx.tma_waits;
-    } else {
-      for (int s = 0; s < NG; ++s) {
-        const int m = min(KA, nr_s[s] - c * KA);
-        if (m <= 0 || st_s[s] != ST_OK) continue;
-        const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KA) * U;
-        for (int e = tid; e < m * U; e += NT) {
-          const int r = e / U, u = e - r * U;
-          *reinterpret_cast<float2 *>(stage + ((size_t)s * KA + r) * RS + 2 * u) = __ldg(src + e);
-        }
-      }
-      __syncthreads();
-    }
-    // two rows (b, b + KA/2) and half of the symbols per thread: each
-    // broadcast z load feeds both rows
-    constexpr int RP = KA / 2;
-    for (int e = tid; e < NG * RP * 2; e += NT) {
-      const int half = e & 1, rp = (e >> 1) % RP, s = (e >> 1) / RP;
-      const int b0 = c * KA + rp, b1 = b0 + RP;
-      if (s >= nact || b0 >= nr_s[s]) continue;
-      const bool has1 = b1 < nr_s[s];
+    for (int s = 0; s < nact && ok; ++s) {
+      if (sk_s[s] || nr_s[s] == 0) continue;
       float2 *Xn = X + (size_t)n_s[s] * K * d.B + lo_s[s];
-      const int k0 = half * Kh, k1 = min(K, k0 + Kh);
       if (st_s[s] != ST_OK) {
-        for (int k = k0; k < k1; ++k) {
-          Xn[(size_t)k * d.B + b0] = make_float2(0.f, 0.f);
-          if (has1) Xn[(size_t)k * d.B + b1] = make_float2(0.f, 0.f);
-        }
+        zero_rows<UP>(nr_s[s], K, X + (size_t)n_s[s] * K * d.B, d.B, lo_s[s], tid);
         continue;
       }
-      const float *hrow[2] = {stage + ((size_t)s * KA + rp) * RS,
-                              stage + ((size_t)s * KA + rp + RP) * RS};
-      float2 *xcol[2] = {Xn + b0, Xn + b1};
-      apply_rows_k<UP, 2>(hrow, has1 ? 2 : 1, Zs + s * K * UP, k0, k1, sc_s[s], xcol, d.B);
+      const float2 *zs = Zs + s * K * UP;
+      // power-of-two normalization of z for the FP16 range
+      float zmax = 0.f;
+      for (int e = tid; e < K * UP; e += NT)
+        zmax = fmaxf(zmax, fmaxf(fabsf(zs[e].x), fabsf(zs[e].y)));
+      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 16));
+      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 8));
+      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 4));
+      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 2));
+      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 1));
+      if (lane == 0) sc_s[NG + warp] = zmax;  // scratch slots after the scales
+      __syncthreads();
+      float zm = 0.f;
+      for (int w = 0; w < NT / 32; ++w) zm = fmaxf(zm, sc_s[NG + w]);
+      int zexp = 0;
+      if (zm > 0.f) frexpf(zm, &zexp);        // zm = f 2^zexp, f in [0.5, 1)
+      const float zn = ldexpf(1.f, -zexp);    // z * zn in (-1, 1)
+      const float out_scale = ldexpf(sc_s[s], zexp);
+      for (int q0 = 0; q0 < K; q0 += 16) {
+        const int nq = min(16, K - q0);
+        // B operands: 32 rows x 8 chunks of 8 entries (4 users x Re/Im)
+        __syncthreads();
+        for (int e = tid; e < 32 * 8; e += NT) {
+          const int row = e >> 3, c8 = e & 7;
+          const int q = row >> 1, im = row & 1;
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int u = 4 * c8 + j;
+            float2 z = make_float2(0.f, 0.f);
+            if (q < nq && u < U && c8 < KCH) z = zs[(q0 + q) * UP + u];
+            z.x *= zn;
+            z.y *= zn;
+            v[2 * j] = im ? z.y : z.x;
+            v[2 * j + 1] = im ? -z.x : z.y;
+          }
+          uint4 hi, lo, hs;
+          uint32_t *ph = &hi.x, *pl = &lo.x, *ps = &hs.x;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+            const float2 hf = __half22float2(h2);
+            const __half2 l2 = __floats2half2_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+            const __half2 s2 = __floats2half2_rn(hf.x * 0x1p-11f, hf.y * 0x1p-11f);
+            ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
+            pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
+            ps[j] = *reinterpret_cast<const uint32_t *>(&s2);
+          }
+          const uint32_t off = tc::sw128_offset(row, c8);
+          *reinterpret_cast<uint4 *>(b_op + off) = hi;
+          *reinterpret_cast<uint4 *>(b_op + BOP + off) = lo;
+          *reinterpret_cast<uint4 *>(b_op + 2 * BOP + off) = hs;
+        }
+        for (int m0 = 0; m0 < nr_s[s] && ok; m0 += 128) {
+          const int mrows = min(128, nr_s[s] - m0);
+          if (m0 > 0) __syncthreads();  // previous tile's readout done
+          // A tiles: rows = antennas, 16-byte chunk c8 = users 4c8..4c8+3
+          const float2 *hsrc = H + ((size_t)n_s[s] * d.B + lo_s[s] + m0) * U;
+          for (int e = tid; e < 128 * KCH; e += NT) {
+            const int r = e / KCH, c8 = e - r * KCH;
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int u = 4 * c8 + j;
+              const float2 h = (r < mrows && u < U) ? __ldg(hsrc + (size_t)r * U + u)
+                                                    : make_float2(0.f, 0.f);
+              v[2 * j] = h.x;
+              v[2 * j + 1] = h.y;
+            }
+            uint4 hi, lo;
+            uint32_t *ph = &hi.x, *pl = &lo.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+              const float2 hf = __half22float2(h2);
+              const __half2 l2 =
+                  __floats2half2_rn((v[2 * j] - hf.x) * 0x1p11f, (v[2 * j + 1] - hf.y) * 0x1p11f);
+              ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
+              pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
+            }
+            const uint32_t off = tc::sw128_offset(r, c8);
+            *reinterpret_cast<uint4 *>(a_hi + off) = hi;
+            *reinterpret_cast<uint4 *>(a_lo + off) = lo;
+          }
+          fence_proxy_async_smem();
+          __syncthreads();
+          if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (int kk = 0; kk < KSTEPS; ++kk) {
+              const uint32_t ko = kk * 32;
+              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko), tc::desc_kmajor_sw128(b_u + ko),
+                          idesc_ap, kk > 0);
+              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko),
+                          tc::desc_kmajor_sw128(b_u + BOP + ko), idesc_ap, true);
+              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_lo_u + ko),
+                          tc::desc_kmajor_sw128(b_u + 2 * BOP + ko), idesc_ap, true);
+            }
+            tc::commit(bar_mma);
+          }
+          ++cx.mma_commits[0];
+          ok = tc_wait_mma(cx, 0);
+          tc::fence_after_sync();
+          if (!ok) break;
+          if (warp < 4) {
+            float v[32];
+            tc::tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16), v);
+            const int r = 32 * warp + lane;
+            if (r < mrows) {
+              float2 *xc = Xn + m0 + r;
+#pragma unroll
+              for (int q = 0; q < 16; ++q)
+                if (q < nq) xc[(size_t)(q0 + q) * d.B] = make_float2(v[2 * q] * out_scale,
+                                                                     v[2 * q + 1] * out_scale);
+            }
+          }
+          tc::fence_before_sync();
+        }
+      }
     }
+    __syncthreads();
   }
   if (!ok) {
     for (int s = 0; s < nact; ++s) {
