@@ -67,9 +67,12 @@ typedef enum {
 
 typedef enum { DP_ZF = 0, DP_WF = 1, DP_FDWF = 2 } dp_mode;
 
-/* Arithmetic of the Gram contraction G_c = H_c H_c^H (Sec. III-B):
- * FP32 SIMT, or tensor cores (tcgen05) with BF16 / FP16 inputs and FP32
- * accumulation.  The solve and the apply are FP32 in every case. */
+/* Arithmetic of the path (Sec. III-B).  DP_FP32: every step in FP32 on the
+ * SIMT cores.  DP_BF16 / DP_FP16: the Gram contraction G_c = H_c H_c^H on the
+ * tensor cores (tcgen05) with BF16 / FP16 inputs and FP32 accumulation; the
+ * solve in FP32; the apply x_c = H_c^H z on the tensor cores as a split-FP16
+ * product (H = H_hi + 2^-11 H_lo, z = z_hi + z_lo, three FP16 products with
+ * FP32 accumulation, about 22 significant bits).  Any U <= 64. */
 typedef enum { DP_FP32 = 0, DP_BF16 = 1, DP_FP16 = 2 } dp_precision;
 
 /* Stream handle; identical to cudaStream_t.  NULL = the legacy default
@@ -148,10 +151,9 @@ dp_status dp_status_get(dp_plan_t plan, int *host_status);
  * independent instances of uneven size (each its own dp_plan_desc: users,
  * antennas, clusters, subcarriers, mode, precision) in persistent launches.
  * Instances are bucketed by kernel family and padded user count: the
- * tensor-core family (prec BF16/FP16 with U <= 32), the FP32 family with the
- * antenna block resident in shared memory, and a streaming remainder;
- * instances with prec BF16/FP16 and U > 32 run the FP32 path (more accurate
- * than requested).  Each bucket is one persistent launch whose CTAs pull
+ * tensor-core family (prec BF16/FP16), the FP32 family with the antenna
+ * block resident in shared memory, the B_c x B_c family (FD-WF clusters with
+ * B_c < U), and a streaming remainder.  Each bucket is one persistent launch whose CTAs pull
  * work items from an atomic queue, largest first; the bucket launches are
  * captured once into a CUDA graph (on a non-NULL stream) and replayed on
  * every call.  Per-instance outputs and status follow the single-plan

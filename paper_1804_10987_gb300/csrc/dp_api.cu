@@ -131,7 +131,7 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
     return DP_ERR_INVALID_ARG;
   if (d.refine != 0 && d.refine != 1) return DP_ERR_INVALID_ARG;
-  // The tensor-core Gram covers up to 32 users; refinement is not built.
+  // The tensor-core path covers up to 64 users; refinement is not built.
   if (d.prec != DP_FP32 && !dp::tc_supported(dp::padded_users(d.U))) return DP_ERR_UNSUPPORTED;
   if (d.refine != 0) return DP_ERR_UNSUPPORTED;
 
@@ -291,6 +291,9 @@ dp_status dp_precode(dp_plan_t p, const void *H, const void *S, void *X) {
     e = dp::launch_fd_small(dp::InstDesc{sd, h, sy, x, p->d_status, nullptr}, p->bcp, p->stream);
     if (e != cudaSuccess || p->all_small) return cuda_status(e);
   }
+  if (p->d.prec != DP_FP32 && dp::pipe_tc_supported(sd, p->UP))
+    return cuda_status(dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, p->d_status,
+                                          nullptr, p->stream));
   if (p->d.prec != DP_FP32)
     return cuda_status(dp::launch_fused_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, p->d_status,
                                            nullptr, p->stream));

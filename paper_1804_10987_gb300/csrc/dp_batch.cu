@@ -276,6 +276,30 @@ void describe(dp_batch *b) {
 
 }  // namespace
 
+namespace dp {
+int resident_blocks(const void *kernel, int threads, size_t dyn_bytes, int tmem_cols) {
+  cudaFuncAttributes a{};
+  int dev = 0, regs_sm = 0, thr_sm = 0, smem_sm = 0, resv = 0, blk_sm = 0;
+  if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) ||
+      cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev) ||
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev)) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int warps = (threads + 31) / 32;
+  int n = std::min(blk_sm, thr_sm / (32 * warps));
+  const int regs_warp = ((a.numRegs * 32 + 255) / 256) * 256;
+  if (regs_warp > 0) n = std::min(n, (regs_sm / regs_warp) / warps);
+  const size_t smem = dyn_bytes + a.sharedSizeBytes + (size_t)resv;
+  n = std::min<size_t>(n, (size_t)smem_sm / smem);
+  if (tmem_cols > 0) n = std::min(n, 512 / tmem_cols);
+  return std::max(n, 0);
+}
+}  // namespace dp
+
 extern "C" {
 
 dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, dp_batch_t *out) {

@@ -410,13 +410,19 @@ __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int 
     const float tr = warp_sum(dg), fro = warp_sum(fr);
     float t = tr - kappa * fro;
     if (kappa * fro > kLemmaMaxRatio * tr) {
+      // the cancelling case: lane i forms (T G)_ij = sum_k T_ik G_kj one
+      // column j at a time (runtime loop: few live registers)
       float part = 0.f;
-#pragma unroll
-      for (int j = 0; j < UP; ++j) {
+#pragma unroll 1
+      for (int j = 0; j < U; ++j) {
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < UP; ++k) cmac(acc, row[k], Gs[k * UP + j]);
-        part = fmaf(acc.x, row[j].x, fmaf(acc.y, row[j].y, part));
+        float2 tij = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jj = 0; jj < UP; ++jj)
+          if (jj == j) tij = row[jj];
+        part = fmaf(acc.x, tij.x, fmaf(acc.y, tij.y, part));
       }
       if (lane >= U) part = 0.f;
       t = warp_sum(part);

@@ -207,11 +207,7 @@ int fd_small_blocks_t(int Kmax) {
       cudaFuncSetAttribute(k_batch_fd_small<BCP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bytes) != cudaSuccess)
     return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_fd_small<BCP>, 32 * FD_WARPS,
-                                                    bytes) != cudaSuccess)
-    return 0;
-  return n;
+  return resident_blocks((const void *)k_batch_fd_small<BCP>, 32 * FD_WARPS, bytes, 0);
 }
 
 }  // namespace

@@ -487,11 +487,7 @@ template <int UP>
 int fused_blocks_t(int maxrows, int Kmax) {
   const size_t bytes = fused_bytes_t<UP>(maxrows, Kmax);
   if (set_smem(k_batch_fused<UP>, bytes) != cudaSuccess) return 0;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_fused<UP>, NT, bytes) !=
-      cudaSuccess)
-    return 0;
-  return n;
+  return resident_blocks((const void *)k_batch_fused<UP>, NT, bytes, 0);
 }
 
 #define DP_DISPATCH_UP(UPV, CALL)                      \

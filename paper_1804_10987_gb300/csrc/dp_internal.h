@@ -11,6 +11,13 @@ namespace dp {
 // Users padded to the kernels' granularity (a multiple of 8, at most 64).
 inline int padded_users(int U) { return ((U + 7) / 8) * 8; }
 
+// CTAs of `kernel` (launched with `threads` threads and `dyn_bytes` of dynamic
+// shared memory, each holding `tmem_cols` TMEM columns) that one SM holds at
+// once, from the limits themselves: threads, registers (allocated per warp in
+// units of 256), shared memory with the per-block reserve, resident blocks,
+// and the 512 TMEM columns.  0 if an attribute query fails.
+int resident_blocks(const void *kernel, int threads, size_t dyn_bytes, int tmem_cols);
+
 // Antenna rows per shared-memory chunk of the streaming Gram / apply kernels.
 int stream_chunk_rows(int UP);
 
@@ -33,7 +40,7 @@ cudaError_t launch_batch_fused(int UP, const InstDesc *insts, const WorkItem *it
                                int *queue, int maxrows, int Kmax, int grid, cudaStream_t s);
 int fused_max_blocks_per_sm(int UP, int maxrows, int Kmax);
 
-// Reduced-precision fused path (tensor-core Gram): users padded to <= 32.
+// Reduced-precision fused path (tensor-core Gram and apply): users padded to <= 64.
 bool tc_supported(int UP);
 cudaError_t launch_fused_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
                             float2 *X, int *status, float *scale_out, cudaStream_t s);
@@ -43,6 +50,11 @@ int tc_systems_per_group(int UP);
 cudaError_t launch_batch_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
                             int n_items, int *queue, int Kmax, int grid, cudaStream_t s);
 int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax);
+// Warp-specialized persistent form of the same arithmetic (bit-identical),
+// for users padded to 8 or 16, 1 <= K <= 16 and bulk-copyable rows.
+bool pipe_tc_supported(const SysDesc &d, int UP);
+cudaError_t launch_pipe_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
+                           float2 *X, int *status, float *scale_out, cudaStream_t s);
 
 // FD-WF clusters with B_c < U (and B_c <= 32) in the B_c x B_c form:
 // padded cluster width (8, 16, 32; 0 if none fits) and the launchers.

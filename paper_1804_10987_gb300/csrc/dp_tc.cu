@@ -41,12 +41,18 @@ struct TcGeo {
   static constexpr int BOP_BYTES = 32 * 128;
   static constexpr int REGION = 2 * TILE_BYTES + 3 * BOP_BYTES;
   // P blocks padded by one float, or XOR-swizzled when that does not fit
-  static constexpr bool P_PAD = (size_t)NG * M2 * (M2 + 1) * 4 <= REGION;
+  // small U: the diagonal P blocks, padded by one float or XOR-swizzled;
+  // U > 32 (one system per CTA): only rows U..2U of P, padded
+  static constexpr bool LARGE = UP > 32;
+  static constexpr bool P_PAD = LARGE || (size_t)NG * M2 * (M2 + 1) * 4 <= REGION;
   static constexpr int PS = P_PAD ? M2 + 1 : M2;
   static_assert(P_PAD || (M2 % 32 == 0), "swizzled P needs 32-float rows");
-  static_assert((size_t)NG * M2 * PS * 4 <= REGION, "P fits the region");
-  static_assert(2 * UP <= 64, "realified users fit one 128-byte K-block");
-  static constexpr int MIN_BLOCKS = UP <= 16 ? 2 : 1;
+  static_assert(LARGE || (size_t)NG * M2 * PS * 4 <= REGION, "P fits the region");
+  static_assert(!LARGE || ((size_t)UP * PS * 4 <= REGION && (size_t)UP * UP * 8 <= REGION),
+                "half of P and the inverse fit the region");
+  // realified users per apply K-block (one 128-byte row of 16-bit entries)
+  static constexpr int KBLK = (2 * UP + 63) / 64;
+  static constexpr int MIN_BLOCKS = UP <= 16 ? 3 : 2;  // U > 32: one system, CTA solve
   __device__ static __forceinline__ int p_index(int s, int r, int c) {
     return (s * M2 + r) * PS + (P_PAD ? c : (c ^ (r & 31)));
   }
@@ -270,36 +276,83 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
     return false;
   }
 
-  // ---- TMEM -> P (the diagonal 2UP x 2UP blocks) ------------------------------
-  if (warp < 4) {
-    const int m = 32 * warp + lane;
-    const int s = m / M2, r = m - s * M2;
+  if constexpr (T::LARGE) {
+    // ---- TMEM -> G for one system with U > 32 ------------------------------
+    // Re G_ij = P[i][j] + P[U'+i][U'+j], Im G_ij = P[U'+i][j] - P[i][U'+j]
+    // (U' = UP): the rows U'..2U' go to shared memory, then the owner of row
+    // i combines its own row with them.
+    float *Pim = P;  // [UP][PS]
+    if (warp < 4) {
+      const int m = 32 * warp + lane;
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      float v[32];
-      tc::tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + 32 * cc, v);
+      for (int cc = 0; cc < 4; ++cc) {
+        float v[32];
+        tc::tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + 32 * cc, v);
+        if (m >= UP && m < M2) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = 32 * cc + j;
-        if (s < NG && n / M2 == s) P[T::p_index(s, r, n - s * M2)] = v[j];
+          for (int j = 0; j < 32; ++j) {
+            const int n = 32 * cc + j;
+            if (n < M2) Pim[(m - UP) * T::PS + n] = v[j];
+          }
+        }
       }
     }
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-
-  // ---- P -> G (Hermitian, lower triangle mirrored) ------------------------------
-  for (int e = tid; e < NG * UP * UP; e += NT) {
-    const int s = e / (UP * UP), ij = e - s * UP * UP, i = ij / UP, j = ij - i * UP;
-    float2 g = make_float2(0.f, 0.f);
-    if (s < nact && i < U && j < U) {
-      const int a = i >= j ? i : j, b = i >= j ? j : i;  // lower-triangle source
-      g.x = P[T::p_index(s, a, b)] + P[T::p_index(s, UP + a, UP + b)];
-      g.y = (a == b) ? 0.f : P[T::p_index(s, UP + a, b)] - P[T::p_index(s, a, UP + b)];
-      if (i < j) g.y = -g.y;
+    for (int e = tid; e < UP * UP; e += NT) Gs[e] = make_float2(0.f, 0.f);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp < 4) {
+      const int m = 32 * warp + lane;
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        float v[32];
+        tc::tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + 32 * cc, v);
+        if (m < U && nact > 0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = 32 * cc + j;
+            if (n < U) {
+              Gs[m * UP + n].x = v[j] + Pim[m * T::PS + UP + n];
+              Gs[m * UP + n].y += Pim[m * T::PS + n];
+            } else if (n >= UP && n < UP + U) {
+              Gs[m * UP + n - UP].y -= v[j];
+            }
+          }
+          if (cc == 3) Gs[m * UP + m].y = 0.f;
+        }
+      }
     }
-    Gs[e] = g;
+    tc::fence_before_sync();
+  } else {
+  // ---- TMEM -> P (the diagonal 2UP x 2UP blocks) ------------------------------
+    if (warp < 4) {
+      const int m = 32 * warp + lane;
+      const int s = m / M2, r = m - s * M2;
+  #pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        float v[32];
+        tc::tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16) + 32 * cc, v);
+  #pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = 32 * cc + j;
+          if (s < NG && n / M2 == s) P[T::p_index(s, r, n - s * M2)] = v[j];
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  
+    // ---- P -> G, row by row ------------------------------------------------------
+    for (int e = tid; e < NG * UP * UP; e += NT) {
+      const int s = e / (UP * UP), ij = e - s * UP * UP, i = ij / UP, j = ij - i * UP;
+      float2 g = make_float2(0.f, 0.f);
+      if (s < nact && i < U && j < U) {
+        g.x = P[T::p_index(s, i, j)] + P[T::p_index(s, UP + i, UP + j)];
+        g.y = (i == j) ? 0.f : P[T::p_index(s, UP + i, j)] - P[T::p_index(s, i, UP + j)];
+      }
+      Gs[e] = g;
+    }
   }
   __syncthreads();
   // per-system finiteness of G (covers H) and of the symbols
@@ -312,15 +365,42 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   }
   __syncthreads();
 
-  // ---- solve: one warp per system --------------------------------------------
-  if (warp < nact) {
+  if constexpr (T::LARGE) {
+    // ---- solve: the whole CTA on the one system (U > 32) ---------------------
+    float2 *Aw = reinterpret_cast<float2 *>(base + L.region);
+    for (int e = tid; e < UP * UP; e += NT) {
+      float2 v = Gs[e];
+      if (e / UP == e % UP) v.x += d.kappa;
+      Aw[e] = v;
+    }
+    __syncthreads();
+    int st = (nact > 0) ? st_s[0] : ST_OK;
     float sc = 0.f;
-    const int st = warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP, Zs + warp * K * UP, UP,
-                                  d.kappa, d.rho2_sys, d.Es, U, K, lane, st_s[warp] == ST_OK,
-                                  sc);
-    if (lane == 0) {
-      st_s[warp] = st;
-      sc_s[warp] = sc;
+    if (nact > 0 && !sk_s[0]) {
+      if (st == ST_OK) st = cta_gj_inverse<UP>(Aw, U, tid);
+      if (st == ST_OK) {
+        const float t = cta_trace_tgt<UP>(Aw, Gs, d.kappa, U, sc_s + NG, tid);
+        if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
+        else sc = sqrtf(d.rho2_sys / (d.Es * t));
+      }
+      if (st == ST_OK) cta_whiten<UP>(Aw, Ss, Zs, U, K, tid);
+    }
+    __syncthreads();
+    if (tid == 0 && nact > 0) {
+      st_s[0] = st;
+      sc_s[0] = sc;
+    }
+  } else {
+  // ---- solve: one warp per system --------------------------------------------
+    if (warp < nact) {
+      float sc = 0.f;
+      const int st = warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP, Zs + warp * K * UP, UP,
+                                    d.kappa, d.rho2_sys, d.Es, U, K, lane, st_s[warp] == ST_OK,
+                                    sc);
+      if (lane == 0) {
+        st_s[warp] = st;
+        sc_s[warp] = sc;
+      }
     }
   }
   fence_proxy_async_smem();
@@ -330,24 +410,16 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   // Per 128-antenna M-tile: D[b][n] = sum_j A[b][j] Bm[n][j] with A[b][2u + r]
   // = (Re, Im) H[b][u] and, for symbol q of a chunk of 16, Bm[2q] = (Re z_u,
   // Im z_u)_u and Bm[2q + 1] = (Im z_u, -Re z_u)_u, so that D[b][2q] + i
-  // D[b][2q + 1] = sum_u conj(H[b][u]) z_q[u].  Split FP16 keeps ~22 bits:
-  // A = A_hi + 2^-11 A_lo, z = z_hi + z_lo, D = A_hi z_hi + A_hi z_lo +
-  // A_lo (2^-11 z_hi); z is first normalized by a power of two per system.
+  // D[b][2q + 1] = sum_u conj(H[b][u]) z_q[u].  The realified users j run in
+  // K-blocks of 64 (one 128-byte swizzled row), accumulated in TMEM.  Split
+  // FP16 keeps ~22 bits: A = A_hi + 2^-11 A_lo, z = z_hi + z_lo, D = A_hi z_hi
+  // + A_hi z_lo + A_lo (2^-11 z_hi); z is first normalized by a power of two.
   {
     unsigned char *a_hi = base + L.region;
     unsigned char *a_lo = a_hi + TILE_BYTES;
     unsigned char *b_op = a_hi + 2 * TILE_BYTES;  // hi, lo, hi * 2^-11
     const uint32_t a_hi_u = smem_u32(a_hi), a_lo_u = smem_u32(a_lo), b_u = smem_u32(b_op);
     const uint32_t idesc_ap = tc::idesc_f16(128, 32, false);
-    constexpr int KCH = (2 * UP + 7) / 8;  // 16-byte chunks of a realified row
-    constexpr int KSTEPS = (2 * UP + 15) / 16;
-    // the chunks of the A tiles beyond the realified row stay zero
-    for (int e = tid; e < 2 * 128 * (8 - KCH); e += NT) {
-      const int t = e / (128 * (8 - KCH)), r = e - t * 128 * (8 - KCH);
-      const int m = r / (8 - KCH), c8 = KCH + r % (8 - KCH);
-      *reinterpret_cast<uint4 *>(a_hi + t * TILE_BYTES + tc::sw128_offset(m, c8)) =
-          make_uint4(0, 0, 0, 0);
-    }
     for (int s = 0; s < nact && ok; ++s) {
       if (sk_s[s] || nr_s[s] == 0) continue;
       float2 *Xn = X + (size_t)n_s[s] * K * d.B + lo_s[s];
@@ -359,12 +431,10 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
       // power-of-two normalization of z for the FP16 range
       float zmax = 0.f;
       for (int e = tid; e < K * UP; e += NT)
-        zmax = fmaxf(zmax, fmaxf(fabsf(zs[e].x), fabsf(zs[e].y)));
-      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 16));
-      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 8));
-      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 4));
-      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 2));
-      zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, 1));
+        if (e % UP < U) zmax = fmaxf(zmax, fmaxf(fabsf(zs[e].x), fabsf(zs[e].y)));
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, o));
+      __syncthreads();
       if (lane == 0) sc_s[NG + warp] = zmax;  // scratch slots after the scales
       __syncthreads();
       float zm = 0.f;
@@ -373,91 +443,97 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
       if (zm > 0.f) frexpf(zm, &zexp);        // zm = f 2^zexp, f in [0.5, 1)
       const float zn = ldexpf(1.f, -zexp);    // z * zn in (-1, 1)
       const float out_scale = ldexpf(sc_s[s], zexp);
-      for (int q0 = 0; q0 < K; q0 += 16) {
+      const float2 *hsys = H + ((size_t)n_s[s] * d.B + lo_s[s]) * U;
+      for (int q0 = 0; q0 < K && ok; q0 += 16) {
         const int nq = min(16, K - q0);
-        // B operands: 32 rows x 8 chunks of 8 entries (4 users x Re/Im)
-        __syncthreads();
-        for (int e = tid; e < 32 * 8; e += NT) {
-          const int row = e >> 3, c8 = e & 7;
-          const int q = row >> 1, im = row & 1;
-          float v[8];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int u = 4 * c8 + j;
-            float2 z = make_float2(0.f, 0.f);
-            if (q < nq && u < U && c8 < KCH) z = zs[(q0 + q) * UP + u];
-            z.x *= zn;
-            z.y *= zn;
-            v[2 * j] = im ? z.y : z.x;
-            v[2 * j + 1] = im ? -z.x : z.y;
-          }
-          uint4 hi, lo, hs;
-          uint32_t *ph = &hi.x, *pl = &lo.x, *ps = &hs.x;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
-            const float2 hf = __half22float2(h2);
-            const __half2 l2 = __floats2half2_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
-            const __half2 s2 = __floats2half2_rn(hf.x * 0x1p-11f, hf.y * 0x1p-11f);
-            ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
-            pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
-            ps[j] = *reinterpret_cast<const uint32_t *>(&s2);
-          }
-          const uint32_t off = tc::sw128_offset(row, c8);
-          *reinterpret_cast<uint4 *>(b_op + off) = hi;
-          *reinterpret_cast<uint4 *>(b_op + BOP + off) = lo;
-          *reinterpret_cast<uint4 *>(b_op + 2 * BOP + off) = hs;
-        }
         for (int m0 = 0; m0 < nr_s[s] && ok; m0 += 128) {
           const int mrows = min(128, nr_s[s] - m0);
-          if (m0 > 0) __syncthreads();  // previous tile's readout done
-          // A tiles: rows = antennas, 16-byte chunk c8 = users 4c8..4c8+3
-          const float2 *hsrc = H + ((size_t)n_s[s] * d.B + lo_s[s] + m0) * U;
-          for (int e = tid; e < 128 * KCH; e += NT) {
-            const int r = e / KCH, c8 = e - r * KCH;
-            float v[8];
+          for (int kb = 0; kb < T::KBLK && ok; ++kb) {
+            const int ent = min(64, 2 * UP - 64 * kb);  // realified entries in this block
+            const int ksteps = (ent + 15) / 16;
+            __syncthreads();  // the previous MMAs and readout are done with A, B, TMEM
+            // B operands: 32 rows x 8 chunks of 8 entries (4 users x Re/Im)
+            for (int e = tid; e < 32 * 8; e += NT) {
+              const int row = e >> 3, c8 = e & 7;
+              const int q = row >> 1, im = row & 1;
+              float v[8];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const int u = 4 * c8 + j;
-              const float2 h = (r < mrows && u < U) ? __ldg(hsrc + (size_t)r * U + u)
-                                                    : make_float2(0.f, 0.f);
-              v[2 * j] = h.x;
-              v[2 * j + 1] = h.y;
-            }
-            uint4 hi, lo;
-            uint32_t *ph = &hi.x, *pl = &lo.x;
+              for (int j = 0; j < 4; ++j) {
+                const int u = 32 * kb + 4 * c8 + j;
+                float2 z = make_float2(0.f, 0.f);
+                if (q < nq && u < U && 8 * c8 < ent) z = zs[(q0 + q) * UP + u];
+                z.x *= zn;
+                z.y *= zn;
+                v[2 * j] = im ? z.y : z.x;
+                v[2 * j + 1] = im ? -z.x : z.y;
+              }
+              uint4 hi, lo, hs;
+              uint32_t *ph = &hi.x, *pl = &lo.x, *ps = &hs.x;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
-              const float2 hf = __half22float2(h2);
-              const __half2 l2 =
-                  __floats2half2_rn((v[2 * j] - hf.x) * 0x1p11f, (v[2 * j + 1] - hf.y) * 0x1p11f);
-              ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
-              pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
+              for (int j = 0; j < 4; ++j) {
+                const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+                const float2 hf = __half22float2(h2);
+                const __half2 l2 = __floats2half2_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+                const __half2 s2 = __floats2half2_rn(hf.x * 0x1p-11f, hf.y * 0x1p-11f);
+                ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
+                ps[j] = *reinterpret_cast<const uint32_t *>(&s2);
+              }
+              const uint32_t off = tc::sw128_offset(row, c8);
+              *reinterpret_cast<uint4 *>(b_op + off) = hi;
+              *reinterpret_cast<uint4 *>(b_op + BOP + off) = lo;
+              *reinterpret_cast<uint4 *>(b_op + 2 * BOP + off) = hs;
             }
-            const uint32_t off = tc::sw128_offset(r, c8);
-            *reinterpret_cast<uint4 *>(a_hi + off) = hi;
-            *reinterpret_cast<uint4 *>(a_lo + off) = lo;
-          }
-          fence_proxy_async_smem();
-          __syncthreads();
-          if (tid == 0) {
+            // A tiles: rows = antennas, 16-byte chunk c8 = users 4c8..4c8+3 of
+            // the block; zero beyond the block's entries and the tile's rows
+            for (int e = tid; e < 128 * 8; e += NT) {
+              const int r = e >> 3, c8 = e & 7;
+              uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
+              if (8 * c8 < ent) {
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const int u = 32 * kb + 4 * c8 + j;
+                  const float2 h = (r < mrows && u < U)
+                                       ? __ldg(hsys + (size_t)(m0 + r) * U + u)
+                                       : make_float2(0.f, 0.f);
+                  v[2 * j] = h.x;
+                  v[2 * j + 1] = h.y;
+                }
+                uint32_t *ph = &hi.x, *pl = &lo.x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+                  const float2 hf = __half22float2(h2);
+                  const __half2 l2 = __floats2half2_rn((v[2 * j] - hf.x) * 0x1p11f,
+                                                       (v[2 * j + 1] - hf.y) * 0x1p11f);
+                  ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                  pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
+                }
+              }
+              const uint32_t off = tc::sw128_offset(r, c8);
+              *reinterpret_cast<uint4 *>(a_hi + off) = hi;
+              *reinterpret_cast<uint4 *>(a_lo + off) = lo;
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+              tc::fence_after_sync();
+              for (int kk = 0; kk < ksteps; ++kk) {
+                const uint32_t ko = kk * 32;
+                tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko),
+                            tc::desc_kmajor_sw128(b_u + ko), idesc_ap, kb > 0 || kk > 0);
+                tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko),
+                            tc::desc_kmajor_sw128(b_u + BOP + ko), idesc_ap, true);
+                tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_lo_u + ko),
+                            tc::desc_kmajor_sw128(b_u + 2 * BOP + ko), idesc_ap, true);
+              }
+              tc::commit(bar_mma);
+            }
+            ++cx.mma_commits[0];
+            ok = tc_wait_mma(cx, 0);
             tc::fence_after_sync();
-#pragma unroll
-            for (int kk = 0; kk < KSTEPS; ++kk) {
-              const uint32_t ko = kk * 32;
-              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko), tc::desc_kmajor_sw128(b_u + ko),
-                          idesc_ap, kk > 0);
-              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko),
-                          tc::desc_kmajor_sw128(b_u + BOP + ko), idesc_ap, true);
-              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_lo_u + ko),
-                          tc::desc_kmajor_sw128(b_u + 2 * BOP + ko), idesc_ap, true);
-            }
-            tc::commit(bar_mma);
           }
-          ++cx.mma_commits[0];
-          ok = tc_wait_mma(cx, 0);
-          tc::fence_after_sync();
           if (!ok) break;
           if (warp < 4) {
             float v[32];
@@ -566,7 +642,7 @@ cudaError_t launch_tc_u(const SysDesc &d, bool bf16, const float2 *H, const floa
 
 }  // namespace
 
-bool tc_supported(int UP) { return UP <= 32; }
+bool tc_supported(int UP) { return UP >= 8 && UP <= 64 && UP % 8 == 0; }
 
 int tc_systems_per_group(int UP) { return UP > 0 && UP <= 64 ? (128 / (2 * UP) > 0 ? 128 / (2 * UP) : 1) : 1; }
 
@@ -581,12 +657,19 @@ cudaError_t launch_batch_tc(int UP, bool bf16, const InstDesc *insts, const Work
     DP_BTC(16)
     DP_BTC(24)
     DP_BTC(32)
+    DP_BTC(40)
+    DP_BTC(48)
+    DP_BTC(56)
+    DP_BTC(64)
     default: return cudaErrorInvalidValue;
   }
 #undef DP_BTC
 }
 
 int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax) {
+  // the occupancy API reports one CTA per SM for these kernels, below what
+  // the SM holds (three CTAs of the U = 16 form were measured resident), so
+  // the count comes from the limits themselves
   int n = 0;
   size_t bytes = 0;
   cudaError_t e = cudaErrorInvalidValue;
@@ -594,19 +677,23 @@ int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax) {
   case UPV:                                                                                   \
     bytes = tc_smem_layout<UPV>(Kmax).total;                                                  \
     if (bf16) {                                                                               \
-      cudaFuncSetAttribute(k_batch_tc<UPV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                           (int)bytes);                                                       \
-      cudaFuncSetAttribute(k_batch_tc<UPV, true>,                                             \
-                           cudaFuncAttributePreferredSharedMemoryCarveout,                    \
-                           (int)cudaSharedmemCarveoutMaxShared);                              \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_tc<UPV, true>, NT, bytes);  \
+      e = cudaFuncSetAttribute(k_batch_tc<UPV, true>,                                         \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);      \
+      if (e == cudaSuccess)                                                                   \
+        e = cudaFuncSetAttribute(k_batch_tc<UPV, true>,                                       \
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,              \
+                                 (int)cudaSharedmemCarveoutMaxShared);                        \
+      if (e == cudaSuccess)                                                                   \
+        n = resident_blocks((const void *)k_batch_tc<UPV, true>, NT, bytes, TMEM_COLS);       \
     } else {                                                                                  \
-      cudaFuncSetAttribute(k_batch_tc<UPV, false>,                                            \
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);          \
-      cudaFuncSetAttribute(k_batch_tc<UPV, false>,                                            \
-                           cudaFuncAttributePreferredSharedMemoryCarveout,                    \
-                           (int)cudaSharedmemCarveoutMaxShared);                              \
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_tc<UPV, false>, NT, bytes); \
+      e = cudaFuncSetAttribute(k_batch_tc<UPV, false>,                                        \
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);      \
+      if (e == cudaSuccess)                                                                   \
+        e = cudaFuncSetAttribute(k_batch_tc<UPV, false>,                                      \
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,              \
+                                 (int)cudaSharedmemCarveoutMaxShared);                        \
+      if (e == cudaSuccess)                                                                   \
+        n = resident_blocks((const void *)k_batch_tc<UPV, false>, NT, bytes, TMEM_COLS);      \
     }                                                                                         \
     break;
   switch (UP) {
@@ -614,6 +701,10 @@ int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax) {
     DP_OCC(16)
     DP_OCC(24)
     DP_OCC(32)
+    DP_OCC(40)
+    DP_OCC(48)
+    DP_OCC(56)
+    DP_OCC(64)
     default: break;
   }
 #undef DP_OCC
@@ -627,6 +718,10 @@ cudaError_t launch_fused_tc(const SysDesc &d, int UP, bool bf16, const float2 *H
     case 16: return launch_tc_u<16>(d, bf16, H, S, X, status, scale_out, s);
     case 24: return launch_tc_u<24>(d, bf16, H, S, X, status, scale_out, s);
     case 32: return launch_tc_u<32>(d, bf16, H, S, X, status, scale_out, s);
+    case 40: return launch_tc_u<40>(d, bf16, H, S, X, status, scale_out, s);
+    case 48: return launch_tc_u<48>(d, bf16, H, S, X, status, scale_out, s);
+    case 56: return launch_tc_u<56>(d, bf16, H, S, X, status, scale_out, s);
+    case 64: return launch_tc_u<64>(d, bf16, H, S, X, status, scale_out, s);
     default: return cudaErrorInvalidValue;
   }
 }

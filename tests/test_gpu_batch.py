@@ -66,12 +66,12 @@ def test_batch_matches_oracle_and_single_plans():
         assert (st[i] == 0).all(), (i, st[i])
         ref = oracle.precode(p.H, p.S, p.cluster_sizes, p.mode, N0=p.N0, tau=p.tau, nthreads=8)
         Xg = Xs[i].cpu().numpy()
-        tol = TOL_FP32 if (prec == "fp32" or p.U > 32) else TOL_LP
+        tol = TOL_FP32 if prec == "fp32" else TOL_LP
         err = rel_err_per_sc(Xg, ref["X"])
         assert err.max() <= tol, (i, p.U, p.B, p.C, p.mode, prec, err.max())
         # the single-plan path runs the same device code
         pl = dp.Plan(p.U, p.B, p.C, p.n_sc, p.K, mode=p.mode,
-                     prec=prec if p.U <= 32 else "fp32", N0=p.N0, tau=p.tau,
+                     prec=prec, N0=p.N0, tau=p.tau,
                      cluster_sizes=p.cluster_sizes)
         X1 = torch.empty_like(Xs[i])
         pl.precode(Hs[i], Ss[i], X1)

@@ -201,9 +201,9 @@ def test_power_normalization_on_gpu():
 def test_fd_small_clusters(U, cs, n_sc, K, snr, prec):
     p = synth.make_problem(U, sum(cs), len(cs), n_sc, K, 64, snr, seed=3000 + U + len(cs),
                            mode="fdwf", cluster_sizes=cs)
-    Xg, st = gpu_precode(p, prec=prec if U <= 32 else "fp32")
+    Xg, st = gpu_precode(p, prec=prec)
     ref = oracle_of(p)  # the oracle takes the B_c x B_c form for B_c < U
     assert np.array_equal(st, ref["status"])
     err = rel_err_per_sc(Xg, ref["X"])
-    tol = TOL_FP32 if (prec == "fp32" or U > 32) else 1e-3
+    tol = TOL_FP32 if prec == "fp32" else 1e-3
     assert err.max() <= tol, err.max()

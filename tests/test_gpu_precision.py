@@ -1,5 +1,5 @@
 """Reduced-precision form: Gram on the tensor cores (BF16 / FP16 inputs, FP32
-accumulation), solve and apply in FP32; against the FP64 oracle at the 1e-3
+accumulation), solve in FP32, apply as a split-FP16 tensor-core product; against the FP64 oracle at the 1e-3
 relative-error bar, i.i.d. and Kronecker-correlated channels."""
 import numpy as np
 import pytest
@@ -70,6 +70,11 @@ def test_c2_shape_modes(prec, mode, tau):
     (6, [3, 90, 40], 4, 2, "fdwf"),       # B_c < U cluster, ragged chunks
     (32, [1000], 3, 14, "wf"),            # 16 chunks of 64 antennas
     (5, [20, 20], 6, 4, "wf"),            # odd U: plain-load staging
+    (40, [96, 100], 3, 5, "wf"),          # U > 32: one system per CTA, 2 K-blocks
+    (64, [300], 2, 14, "wf"),             # 128 realified rows fill the tile
+    (48, [128, 128, 256], 2, 40, "fdwf"), # 3 symbol chunks of 16, ragged
+    (57, [700, 324], 2, 64, "wf"),        # U pads to 64, K at its maximum
+    (33, [64, 64], 5, 3, "fdwf"),         # U pads to 40
 ])
 def test_tc_shapes(U, cs, n_sc, K, mode):
     p = synth.make_problem(U, sum(cs), len(cs), n_sc, K, 16, 12.0, seed=2000 + U + n_sc,
@@ -107,3 +112,36 @@ def test_fp16_more_accurate_than_bf16():
     ef = check(p, "fp16")
     assert np.median(ef) < np.median(eb)
     _ = to_dev
+
+
+@pytest.mark.parametrize("U,cs,n_sc,K,mode,prec", [
+    (16, [32] * 8, 1203, 14, "wf", "fp16"),      # 256 antennas, ragged last group
+    (16, [32] * 8, 300, 14, "fdwf", "bf16"),     # one system per cluster
+    (12, [100, 156], 37, 16, "wf", "fp16"),      # U < padded users, K at the limit
+    (8, [64, 64], 101, 7, "zf", "fp16"),         # 8 systems per group
+    (6, [3, 90, 40, 5], 23, 1, "fdwf", "fp16"),  # B_c < U clusters go elsewhere, K = 1
+    (16, [700, 300], 9, 3, "wf", "bf16"),        # apply tiles with ragged tails
+])
+def test_pipelined_kernel_matches_group_kernel(U, cs, n_sc, K, mode, prec):
+    """A single plan runs the warp-specialized persistent kernel, a batch of
+    one runs the group kernel: the same arithmetic, so the same bits."""
+    import torch
+    p = synth.make_problem(U, sum(cs), len(cs), n_sc, K, 16, 10.0, seed=4000 + U + n_sc,
+                           mode=mode, cluster_sizes=cs)
+    H, S = to_dev(p.H), to_dev(p.S)
+    pl = dp.Plan(p.U, p.B, p.C, p.n_sc, p.K, mode=mode, prec=prec, N0=p.N0, tau=p.tau,
+                 cluster_sizes=cs)
+    X1 = pl.empty("X")
+    pl.precode(H, S, X1)
+    st1 = pl.status_get()
+    b = dp.Batch([dict(U=p.U, B=p.B, C=p.C, n_sc=p.n_sc, K=p.K, mode=mode, prec=prec, rho2=p.rho2,
+                       N0=p.N0, Es=p.Es, tau=p.tau, cluster_sizes=cs)])
+    X2 = torch.full_like(X1, float("nan"))
+    b.precode([H], [S], [X2])
+    st2 = b.status_get()[0]
+    torch.cuda.synchronize()
+    assert np.array_equal(st1, st2) and (st1 == 0).all()
+    assert torch.equal(X1, X2)
+    if mode != "zf":
+        ref = oracle_of(p)
+        assert rel_err_per_sc(X1.cpu().numpy(), ref["X"]).max() <= TOL_LP

@@ -73,7 +73,7 @@ def test_alone_equals_mix_and_matches_oracle():
         p, desc, _ = cells[c]
         ref = oracle.precode(p.H, S[i].cpu().numpy(), p.cluster_sizes, desc["mode"], N0=p.N0,
                              tau=0.125, nthreads=8)
-        tol = TOL_FP32 if (desc["prec"] == "fp32" or p.U > 32) else TOL_LP
+        tol = TOL_FP32 if desc["prec"] == "fp32" else TOL_LP
         assert rel_err_per_sc(alone[i].cpu().numpy(), ref["X"]).max() <= tol
     srv.close()
 
