@@ -345,6 +345,134 @@ __device__ bool load_symbols(const float2 *__restrict__ Sn, float2 *Ss, int U, i
   return __syncthreads_and(fin) != 0;
 }
 
+// ------------------------------------------------ lane-segment reductions ---
+// Butterflies over aligned segments of SEG lanes (SEG a power of two <= 32).
+template <int SEG>
+__device__ __forceinline__ float seg_sum(float v) {
+#pragma unroll
+  for (int o = SEG / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+template <int SEG>
+__device__ __forceinline__ float seg_max(float v) {
+#pragma unroll
+  for (int o = SEG / 2; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+
+// ------------------------------------------------- split-row warp solve ---
+// A system of UP <= 16 padded users on a segment of SEG = 2 UP lanes: lane
+// (i, h) = segment lane h UP + i holds columns [h UP/2, (h + 1) UP/2) of row
+// i of A = G + kappa I.  Gauss-Jordan without pivoting (A is Hermitian
+// positive definite), then t = tr(T G T) by Lemma 1 (by its definition,
+// sum_ij (T G)_ij conj(T_ij), where kappa ||T||_F^2 comes close to tr(T)),
+// scale = sqrt(rho2 / (Es t)) (Thm. 1) and z_k = T s_k.  Gw: G [UP][UP]
+// (zero pads) for the definition; Ss: s_k at Ss[k UP + u] (zero pads);
+// z_k[i] goes to zout[k ldz + i] (i < U) from lanes with h = 0 when store is
+// set -- zout may be Ss itself.  zmax: max |Re|, |Im| over the system's z.
+// Every lane of the warp takes part (with UP = 8 both segments run in step).
+template <int UP>
+__device__ __forceinline__ int split_solve(float2 (&row)[UP / 2], const float2 *Gw,
+                                           const float2 *Ss, float2 *zout, int ldz, float kappa,
+                                           float rho2, float Es, int U, int K, int sl,
+                                           bool finite_in, bool store, float &scale,
+                                           float &zmax) {
+  constexpr int HALF = UP / 2, SEG = 2 * UP;
+  static_assert(SEG <= 32, "a system fits a warp");
+  const int i = sl % UP, h = sl / UP;
+  int st = finite_in ? ST_OK : ST_NONFINITE;
+  bool bad = false;
+#pragma unroll
+  for (int p = 0; p < UP; ++p) {
+    if (p >= U) break;
+    const int hp = p / HALF, pc = p % HALF;
+    const float piv = __shfl_sync(FULL, row[pc].x, p + hp * UP, SEG);
+    bad = bad || !(piv > 0.f) || !isfinite(piv);
+    const float ip = 1.f / piv;
+    float2 oth;  // A_ip sits in half hp: this lane's or its partner's
+    oth.x = __shfl_xor_sync(FULL, row[pc].x, UP, SEG);
+    oth.y = __shfl_xor_sync(FULL, row[pc].y, UP, SEG);
+    const float2 f = cscale(h == hp ? row[pc] : oth, ip);
+    const int src = p + h * UP;  // row p, this lane's half
+#pragma unroll
+    for (int jj = 0; jj < HALF; ++jj) {
+      float2 rp;
+      rp.x = __shfl_sync(FULL, row[jj].x, src, SEG);
+      rp.y = __shfl_sync(FULL, row[jj].y, src, SEG);
+      const int j = h * HALF + jj;
+      if (i == p) {
+        row[jj] = (j == p) ? make_float2(ip, 0.f) : cscale(rp, ip);
+      } else if (j == p) {
+        row[jj] = make_float2(-f.x, -f.y);
+      } else {
+        cmsub(row[jj], f, rp);
+      }
+    }
+  }
+  if (st == ST_OK && bad) st = ST_NOT_PD;
+  float sc = 0.f;
+  {
+    float dg = 0.f, fr = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < HALF; ++jj) {
+      if (h * HALF + jj == i) dg = row[jj].x;
+      fr = fmaf(row[jj].x, row[jj].x, fmaf(row[jj].y, row[jj].y, fr));
+    }
+    if (i >= U) {
+      dg = 0.f;
+      fr = 0.f;
+    }
+    const float tr = seg_sum<SEG>(dg), fro = seg_sum<SEG>(fr);
+    float t = tr - kappa * fro;
+    const bool need = kappa * fro > kLemmaMaxRatio * tr;
+    if (__any_sync(FULL, need && st == ST_OK)) {
+      // (T G)_ij from both halves of row i of T, one column j at a time
+      float part = 0.f;
+#pragma unroll 1
+      for (int j = 0; j < U; ++j) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int kk = 0; kk < HALF; ++kk) cmac(acc, row[kk], Gw[(h * HALF + kk) * UP + j]);
+        float2 oth;
+        oth.x = __shfl_xor_sync(FULL, acc.x, UP, SEG);
+        oth.y = __shfl_xor_sync(FULL, acc.y, UP, SEG);
+        const float2 tg = cadd(acc, oth);
+        if (j / HALF == h) {
+          float2 tij = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int jj = 0; jj < HALF; ++jj)
+            if (h * HALF + jj == j) tij = row[jj];
+          part = fmaf(tg.x, tij.x, fmaf(tg.y, tij.y, part));
+        }
+      }
+      if (i >= U) part = 0.f;
+      const float talt = seg_sum<SEG>(part);
+      if (need) t = talt;
+    }
+    if (st == ST_OK) {
+      if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
+      else sc = sqrtf(rho2 / (Es * t));
+    }
+  }
+  float zm = 0.f;
+  for (int k = 0; k < K; ++k) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (st == ST_OK) {
+#pragma unroll
+      for (int jj = 0; jj < HALF; ++jj) cmac(acc, row[jj], Ss[k * UP + h * HALF + jj]);
+    }
+    float2 oth;
+    oth.x = __shfl_xor_sync(FULL, acc.x, UP, SEG);
+    oth.y = __shfl_xor_sync(FULL, acc.y, UP, SEG);
+    const float2 z = cadd(acc, oth);
+    if (i < U) zm = fmaxf(zm, fmaxf(fabsf(z.x), fabsf(z.y)));
+    if (store && h == 0 && i < U) zout[(size_t)k * ldz + i] = z;
+  }
+  zmax = seg_max<SEG>(zm);
+  scale = sc;
+  return st;
+}
+
 // ----------------------------------------------------- warp-per-system solve ---
 // Lane i holds row i of A = G + kappa I (UP complex registers).  In-place
 // Gauss-Jordan without pivoting (A Hermitian positive definite: the pivots are
@@ -375,8 +503,8 @@ __device__ __forceinline__ bool warp_gj_inverse(float2 (&row)[UP], int lane, int
   return true;
 }
 
-// One system solved by one warp (steps a3-a5): lane i holds row i of
-// A = G + kappa I; Gauss-Jordan inverse in registers, t = tr(T G T), scale =
+// One system solved by one warp (steps a3-a5); up to 16 padded users in the
+// split-row form above, else lane i holds row i of A = G + kappa I; Gauss-Jordan inverse in registers, t = tr(T G T), scale =
 // sqrt(rho2 / (Es t)), z_k = T s_k written to zout[k * ldz + i] (i < U).
 // Gs [UP][UP] and Ss [K][UP] in shared memory with zero pads.  Returns the
 // status; on failure z = 0 and scale = 0.
@@ -384,6 +512,20 @@ template <int UP>
 __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int ldz, float kappa,
                           float rho2, float Es, int U, int K, int lane, bool finite_in,
                           float &scale) {
+  if constexpr (2 * UP <= 32) {  // split rows over 2 UP lanes
+    constexpr int HALF = UP / 2, SEG = 2 * UP;
+    const int sl = lane % SEG, i = sl % UP, h = sl / UP;
+    float2 row[HALF];
+#pragma unroll
+    for (int jj = 0; jj < HALF; ++jj) {
+      const int j = h * HALF + jj;
+      row[jj] = (i < U) ? Gs[i * UP + j] : make_float2(0.f, 0.f);
+      if (j == i) row[jj].x += kappa;
+    }
+    float zm;
+    return split_solve<UP>(row, Gs, Ss, zout, ldz, kappa, rho2, Es, U, K, sl, finite_in,
+                           lane < SEG, scale, zm);
+  }
   float2 row[UP];
 #pragma unroll
   for (int j = 0; j < UP; ++j) {

@@ -19,8 +19,9 @@
 //                          mbarriers;
 //   MMA issuer (warp 13)   one thread issues every tcgen05.mma and commit;
 //   solvers   (warps 8-11) TMEM -> G in registers (one system per 2 UP
-//                          lanes), Gauss-Jordan inverse, t, scale, z = T s;
-//                          z and scale to shared memory.
+//                          lanes, each lane half a row), Gauss-Jordan
+//                          inverse, t, scale, z = T s; z and scale to
+//                          shared memory.
 //
 // The solve of group g thus runs while the converters apply group g - 1 and
 // stream the Gram of group g + 1, and the next groups' H is always in flight.
@@ -78,10 +79,9 @@ struct PpGeo {
   static constexpr int GOP = RAW + PP_NRAW * PP_RAW;            // 2 Gram operand tiles
   static constexpr int AOP = GOP + 2 * PP_TILE;                 // 2 apply tiles [hi | lo]
   static constexpr int BOPS = AOP + 2 * PP_TILE;                // 2 x (hi, lo, hi 2^-11)
-  static constexpr int SS = BOPS + 2 * 3 * PP_BOP;              // S per solver system
-  static constexpr int GS = SS + NG * PP_KMAX * UP * 8;         // G per solver system
-  static constexpr int ZS = GS + NG * UP * UP * 8;              // 2 x NG x [K][UP]
-  static constexpr int INFO = ZS + 2 * NG * PP_KMAX * UP * 8;   // st, sc, zexp: 2 x NG each
+  static constexpr int GS = BOPS + 2 * 3 * PP_BOP;              // G per solver system
+  static constexpr int SZ = GS + NG * UP * UP * 8;              // s, then z: 2 x NG x [K][UP]
+  static constexpr int INFO = SZ + 2 * NG * PP_KMAX * UP * 8;   // st, sc, zexp: 2 x NG each
   static constexpr int BARS = INFO + 3 * 2 * NG * 4;
   static constexpr int MISC = BARS + B_COUNT * 8;               // tmem base, abort, per-warp done
   static constexpr int BYTES = MISC + 48 + 1024;                // + alignment slack
@@ -105,18 +105,6 @@ __device__ __forceinline__ bool bar_and(int id, int n, bool v) {
   return r != 0;
 }
 
-template <int SEG>
-__device__ __forceinline__ float seg_sum(float v) {
-#pragma unroll
-  for (int o = SEG / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v;
-}
-template <int SEG>
-__device__ __forceinline__ float seg_max(float v) {
-#pragma unroll
-  for (int o = SEG / 2; o >= 1; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
-  return v;
-}
 // AND of a predicate over this lane's segment of SEG lanes.
 template <int SEG>
 __device__ __forceinline__ bool seg_all(bool v, int lane) {
@@ -284,7 +272,7 @@ __device__ void pp_converter(const InstDesc &in, int ngroups, unsigned char *bas
   const int *st_i = reinterpret_cast<const int *>(base + T::INFO);
   const float *sc_i = reinterpret_cast<const float *>(base + T::INFO + 2 * NG * 4);
   const int *ze_i = reinterpret_cast<const int *>(base + T::INFO + 4 * NG * 4);
-  const float2 *Zs = reinterpret_cast<const float2 *>(base + T::ZS);
+  const float2 *Zs = reinterpret_cast<const float2 *>(base + T::SZ);
   uint32_t raw_i = 0, gop_i = 0, tile_i = 0, bsys_i = 0;
   int o = 0, prev = -1;
   bool run = true;
@@ -561,41 +549,49 @@ __device__ void pp_issuer(const InstDesc &in, int ngroups, unsigned char *base, 
 }
 
 // --------------------------------------------------------------- solver ---
+// Solver warp sw takes systems sw * SPW .. of each group, one per segment of
+// 2 UP lanes in the split-row form: lane (i, h) holds half h of row i.  The
+// system's symbols are loaded into its z buffer, which the whitening then
+// overwrites with z.
 template <int UP>
 __device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, uint64_t *bars,
                           uint32_t taddr, volatile int *abort_f) {
   using T = PpGeo<UP>;
-  constexpr int NG = T::NG, SEG = T::SEG, SPW = T::SPW;
+  constexpr int NG = T::NG, SEG = T::SEG, SPW = T::SPW, HALF = UP / 2;
   const SysDesc &d = in.d;
   const int total = d.n_sc * d.nsys;
   const int U = d.U, K = d.K;
   const float kappa = d.kappa;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sw = warp - PP_CV, stid = tid - 32 * PP_CV;  // solver warp, thread
-  const int seg = lane / SEG, sl = lane % SEG;
+  const int seg = lane / SEG, sl = lane % SEG, i = sl % UP, h = sl / UP;
   const int sysi = sw * SPW + seg;  // this lane's system within the group
-  float2 *Ssw = reinterpret_cast<float2 *>(base + T::SS) + (size_t)sysi * PP_KMAX * UP;
   float2 *Gw = reinterpret_cast<float2 *>(base + T::GS) + (size_t)sysi * UP * UP;
-  float2 *Zs = reinterpret_cast<float2 *>(base + T::ZS);
   int *st_i = reinterpret_cast<int *>(base + T::INFO);
   float *sc_i = reinterpret_cast<float *>(base + T::INFO + 2 * NG * 4);
   int *ze_i = reinterpret_cast<int *>(base + T::INFO + 4 * NG * 4);
   int o = 0;
   for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
     if (pp_group_rows<UP>(d, total, g) == 0) continue;
-    const int sys = g * NG + sysi;
+    const int sys = g * NG + sysi, zb = o & 1;
     const PpSys y = pp_sys(d, total, sys);
+    float2 *Sz = reinterpret_cast<float2 *>(base + T::SZ) + (size_t)(zb * NG + sysi) * PP_KMAX * UP;
+    // the converters are done with this buffer's previous group (o - 2)
+    bool w = !*abort_f;
+    if (w && o >= 2) w = mbar_wait(&bars[B_ZFREE + zb], ((o >> 1) - 1) & 1);
     // symbols of this system (zero pads), fetched while the Gram runs
     bool fin_s = true;
-    for (int e = sl; e < K * UP; e += SEG) {
-      const int k = e / UP, u = e - k * UP;
-      float2 v = make_float2(0.f, 0.f);
-      if (y.live && u < U) v = __ldg(in.S + ((size_t)y.n * K + k) * U + u);
-      fin_s = fin_s && cfinite(v);
-      Ssw[k * UP + u] = v;
+    if (w) {
+      for (int e = sl; e < K * UP; e += SEG) {
+        const int k = e / UP, u = e - k * UP;
+        float2 v = make_float2(0.f, 0.f);
+        if (y.live && u < U) v = __ldg(in.S + ((size_t)y.n * K + k) * U + u);
+        fin_s = fin_s && cfinite(v);
+        Sz[k * UP + u] = v;
+      }
     }
     // this warp's 32 rows of P (its systems' diagonal blocks)
-    bool w = !*abort_f && mbar_wait(&bars[B_GRAMDONE], o & 1);
+    if (w) w = mbar_wait(&bars[B_GRAMDONE], o & 1);
     w = __all_sync(FULL, w) != 0;
     float v[32];
     if (w) {
@@ -612,140 +608,47 @@ __device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, 
     }
     if (stid == 0) mbar_arrive(&bars[B_GRAMFREE]);
 
-    // G row i (lane i of the segment): Re G_ij = P_ij + P_{U'+i,U'+j},
-    // Im G_ij = P_{U'+i,j} - P_{i,U'+j} with U' = UP; row U'+i comes from
-    // lane U'+i of the segment
+    // half h of G row i: Re G_ij = P_ij + P_{U'+i,U'+j}, Im G_ij = P_{U'+i,j} -
+    // P_{i,U'+j} (U' = UP).  Lane (i, 0) holds TMEM row i, lane (i, 1) row
+    // U' + i; each sends the partner the two entries of the partner's half.
     float pw[SEG];
 #pragma unroll
     for (int c = 0; c < SEG; ++c) pw[c] = (SEG == 32 || seg == 0) ? v[c] : v[(SEG % 32) + c];
-    float2 row[UP];
+    float2 row[HALF];
     bool fin_g = true;
 #pragma unroll
-    for (int j = 0; j < UP; ++j) {
-      const float a = __shfl_down_sync(FULL, pw[UP + j], UP, SEG);
-      const float b = __shfl_down_sync(FULL, pw[j], UP, SEG);
+    for (int jj = 0; jj < HALF; ++jj) {
+      const float s1 = h == 0 ? pw[HALF + jj] : pw[UP + jj];
+      const float s2 = h == 0 ? pw[UP + HALF + jj] : pw[jj];
+      const float r1 = __shfl_xor_sync(FULL, s1, UP, SEG);
+      const float r2 = __shfl_xor_sync(FULL, s2, UP, SEG);
+      const int j = h * HALF + jj;
+      const float re = h == 0 ? pw[jj] + r1 : r1 + pw[UP + HALF + jj];
+      const float im = h == 0 ? r2 - pw[UP + jj] : pw[HALF + jj] - r2;
       float2 gij = make_float2(0.f, 0.f);
-      if (sl < U && j < U) gij = make_float2(pw[j] + a, (j == sl) ? 0.f : b - pw[UP + j]);
+      if (i < U && j < U) gij = make_float2(re, j == i ? 0.f : im);
       fin_g = fin_g && cfinite(gij);
-      row[j] = gij;
+      Gw[i * UP + j] = gij;
+      row[jj] = gij;
+      if (j == i) row[jj].x += kappa;
     }
-    if (sl < UP) {
-#pragma unroll
-      for (int j = 0; j < UP; ++j) Gw[sl * UP + j] = row[j];
-    }
-#pragma unroll
-    for (int j = 0; j < UP; ++j)
-      if (j == sl) row[j].x += kappa;
     __syncwarp();
     const bool finite_in = seg_all<SEG>(fin_s && fin_g, lane);
-
-    // Gauss-Jordan inverse in place (no pivoting: A is positive definite);
-    // a bad pivot only flags the segment so that both segments stay in step
-    int st = finite_in ? ST_OK : ST_NONFINITE;
-    bool bad = false;
-#pragma unroll
-    for (int p = 0; p < UP; ++p) {
-      if (p >= U) break;
-      const float piv = __shfl_sync(FULL, row[p].x, p, SEG);
-      bad = bad || !(piv > 0.f) || !isfinite(piv);
-      const float ip = 1.f / piv;
-      const float2 f = cscale(row[p], ip);
-#pragma unroll
-      for (int j = 0; j < UP; ++j) {
-        float2 rp;
-        rp.x = __shfl_sync(FULL, row[j].x, p, SEG);
-        rp.y = __shfl_sync(FULL, row[j].y, p, SEG);
-        if (sl == p) {
-          row[j] = (j == p) ? make_float2(ip, 0.f) : cscale(rp, ip);
-        } else if (j == p) {
-          row[j] = make_float2(-f.x, -f.y);
-        } else {
-          cmsub(row[j], f, rp);
-        }
-      }
-    }
-    if (st == ST_OK && bad) st = ST_NOT_PD;
-
-    // t = tr(T G T) by Lemma 1, or by its definition where Lemma 1 cancels
-    float sc = 0.f;
-    {
-      float dg = 0.f, fr = 0.f;
-#pragma unroll
-      for (int j = 0; j < UP; ++j) {
-        if (j == sl) dg = row[j].x;
-        fr = fmaf(row[j].x, row[j].x, fmaf(row[j].y, row[j].y, fr));
-      }
-      if (sl >= U) {
-        dg = 0.f;
-        fr = 0.f;
-      }
-      const float tr = seg_sum<SEG>(dg), fro = seg_sum<SEG>(fr);
-      float t = tr - kappa * fro;
-      const bool need = kappa * fro > kLemmaMaxRatio * tr;
-      if (__any_sync(FULL, need && st == ST_OK)) {
-        float part = 0.f;
-#pragma unroll 1
-        for (int j = 0; j < U; ++j) {
-          float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int k = 0; k < UP; ++k) cmac(acc, row[k], Gw[k * UP + j]);
-          float2 tij = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int jj = 0; jj < UP; ++jj)
-            if (jj == j) tij = row[jj];
-          part = fmaf(acc.x, tij.x, fmaf(acc.y, tij.y, part));
-        }
-        if (sl >= U) part = 0.f;
-        const float talt = seg_sum<SEG>(part);
-        if (need) t = talt;
-      }
-      if (st == ST_OK) {
-        if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-        else sc = sqrtf(d.rho2_sys / (d.Es * t));
-      }
-    }
-    // z_k = T s_k, and the power of two that normalizes z for FP16
-    float2 zr[PP_KMAX];
-    float zm = 0.f;
-#pragma unroll
-    for (int k = 0; k < PP_KMAX; ++k) {
-      float2 acc = make_float2(0.f, 0.f);
-      if (k < K && st == ST_OK) {
-#pragma unroll
-        for (int j = 0; j < UP; ++j) cmac(acc, row[j], Ssw[k * UP + j]);
-      }
-      zr[k] = acc;
-      if (k < K && sl < U) zm = fmaxf(zm, fmaxf(fabsf(acc.x), fabsf(acc.y)));
-    }
-    zm = seg_max<SEG>(zm);
+    float sc = 0.f, zm = 0.f;
+    const int st = split_solve<UP>(row, Gw, Sz, Sz, UP, kappa, d.rho2_sys, d.Es, U, K, sl,
+                                   finite_in, true, sc, zm);
     int zexp = 0;
     if (zm > 0.f) frexpf(zm, &zexp);
-
-    // hand over: z, scale and status of group o (buffer o % 2)
-    const int zb = o & 1;
-    bool wz = !*abort_f;
-    if (wz && o >= 2) wz = mbar_wait(&bars[B_ZFREE + zb], ((o >> 1) - 1) & 1);
-    if (wz) {
-      float2 *zo = Zs + (size_t)(zb * NG + sysi) * PP_KMAX * UP;
-      if (sl < U) {
-#pragma unroll
-        for (int k = 0; k < PP_KMAX; ++k)
-          if (k < K) zo[k * UP + sl] = zr[k];
-      }
-      if (sl == 0) {
-        st_i[zb * NG + sysi] = st;
-        sc_i[zb * NG + sysi] = sc;
-        ze_i[zb * NG + sysi] = zexp;
-        if (y.live) {
-          in.status[sys] = st;
-          if (in.scale_out) in.scale_out[sys] = st == ST_OK ? sc : 0.f;
-        }
+    if (sl == 0) {
+      st_i[zb * NG + sysi] = st;
+      sc_i[zb * NG + sysi] = sc;
+      ze_i[zb * NG + sysi] = zexp;
+      if (y.live) {
+        in.status[sys] = st;
+        if (in.scale_out) in.scale_out[sys] = st == ST_OK ? sc : 0.f;
       }
     }
-    if (!bar_and(BAR_SV, 32 * PP_SV, wz)) {
-      *abort_f = 1;
-      break;
-    }
+    if (!bar_and(BAR_SV, 32 * PP_SV, true)) break;
     if (stid == 0) mbar_arrive(&bars[B_ZREADY + zb]);
     ++o;
   }
