@@ -34,7 +34,7 @@ WORKLOAD = dict(name="c2", U=16, B=256, C=8, n_sc=1200, K=14, qam=16, snr_db=10.
 KERNEL_SOURCES = {
     "fp32": ["paper_1804_10987_gb300/csrc/dp_fp32.cu", "paper_1804_10987_gb300/csrc/dp_blocks.cuh",
              "paper_1804_10987_gb300/csrc/dp_common.cuh"],
-    "tc": ["paper_1804_10987_gb300/csrc/dp_tc.cu", "paper_1804_10987_gb300/csrc/dp_tc.cuh",
+    "tc": ["paper_1804_10987_gb300/csrc/dp_tcpipe.cu", "paper_1804_10987_gb300/csrc/dp_tc.cuh",
            "paper_1804_10987_gb300/csrc/dp_blocks.cuh", "paper_1804_10987_gb300/csrc/dp_common.cuh"],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
@@ -77,7 +77,9 @@ def metric_name(mode):
 
 
 def kernel_name(prec):
-    return "k_fused<16>" if prec == "fp32" else f"k_fused_tc<16,{'bf16' if prec == 'bf16' else 'fp16'}>"
+    """The one kernel of a single-plan launch on this workload (U = 16, K = 14):
+    the FP32 fused kernel, or the warp-specialized tensor-core kernel."""
+    return "k_fused<16>" if prec == "fp32" else f"k_pipe_tc<16,{'bf16' if prec == 'bf16' else 'fp16'}>"
 
 
 def config_dict(args, world, slots):
