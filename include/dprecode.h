@@ -140,6 +140,24 @@ dp_status dp_precode_apply(dp_plan_t plan, const void *H, const void *Z, const f
  * precision selects the Gram arithmetic. */
 dp_status dp_precode(dp_plan_t plan, const void *H, const void *S, void *X);
 
+/* dp_precode for arrays in HOST memory (the slot arrives from and leaves to
+ * host memory, Sec. IV-B's end-to-end setting).  H [n_sc][B][U], S
+ * [n_sc][K][U] and X [n_sc][K][B] are host pointers, with the dp_precode
+ * layouts; page-locked memory (cudaHostAlloc / cudaHostRegister) lets the
+ * copies overlap, pageable memory works without overlap.  The subcarriers
+ * go in chunks of chunk_sc (<= 0: n_sc / 8 rounded up, at least 1): chunk
+ * i's upload of H and S, its precoding and its download of X run on three
+ * streams through a 3-deep ring of device staging buffers that the plan
+ * allocates on first use (3 chunks of H, S and X; freed with the plan), so
+ * that uploads, kernels and downloads of consecutive chunks overlap.
+ * Results and per-subcarrier status equal those of dp_precode bit for bit.
+ * The call returns once everything is enqueued; it is ordered after the
+ * work already on the plan's stream and completes on that stream
+ * (synchronize it, or call dp_status_get, before reading X).  The host
+ * arrays must stay valid until then.  DP_ERR_OOM if the staging buffers
+ * cannot be allocated. */
+dp_status dp_precode_host(dp_plan_t plan, const void *H, const void *S, void *X, int chunk_sc);
+
 /* Wait for the plan's stream and copy the per-subcarrier status of the last
  * call that wrote it into host_status[n_sc] (host memory; may be NULL).
  * Returns the first non-DP_OK entry (DP_OK if all succeeded). */

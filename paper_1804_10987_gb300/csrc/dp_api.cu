@@ -28,6 +28,14 @@ struct dp_plan {
   float2 *w_G = nullptr;
   float2 *w_Z = nullptr;
   float *w_scale = nullptr;
+  // dp_precode_host: 3-deep ring of device staging chunks, copy streams and
+  // the events that order them (allocated on first use)
+  static constexpr int NSTAGE = 3;
+  int hp_chunk = 0;
+  float2 *hp_H = nullptr, *hp_S = nullptr, *hp_X = nullptr;
+  cudaStream_t hp_up = nullptr, hp_down = nullptr;
+  cudaEvent_t hp_start = nullptr;
+  cudaEvent_t hp_up_done[NSTAGE] = {}, hp_calc_done[NSTAGE] = {}, hp_down_done[NSTAGE] = {};
 };
 
 namespace {
@@ -83,6 +91,56 @@ dp_status ensure_workspace(dp_plan *p) {
     cudaGetLastError();
     return DP_ERR_OOM;
   }
+  return DP_OK;
+}
+
+void free_host_pipeline(dp_plan *p) {
+  if (p->hp_up) cudaStreamSynchronize(p->hp_up);
+  if (p->hp_down) cudaStreamSynchronize(p->hp_down);
+  cudaFree(p->hp_H);
+  cudaFree(p->hp_S);
+  cudaFree(p->hp_X);
+  p->hp_H = p->hp_S = p->hp_X = nullptr;
+  for (int b = 0; b < dp_plan::NSTAGE; ++b) {
+    if (p->hp_up_done[b]) cudaEventDestroy(p->hp_up_done[b]);
+    if (p->hp_calc_done[b]) cudaEventDestroy(p->hp_calc_done[b]);
+    if (p->hp_down_done[b]) cudaEventDestroy(p->hp_down_done[b]);
+    p->hp_up_done[b] = p->hp_calc_done[b] = p->hp_down_done[b] = nullptr;
+  }
+  if (p->hp_start) cudaEventDestroy(p->hp_start);
+  if (p->hp_up) cudaStreamDestroy(p->hp_up);
+  if (p->hp_down) cudaStreamDestroy(p->hp_down);
+  p->hp_start = nullptr;
+  p->hp_up = p->hp_down = nullptr;
+  p->hp_chunk = 0;
+  cudaGetLastError();
+}
+
+// Staging ring for chunks of `chunk` subcarriers (kept if already as large).
+dp_status ensure_host_pipeline(dp_plan *p, int chunk) {
+  if (p->hp_chunk >= chunk) return DP_OK;
+  if (p->hp_chunk) {  // earlier calls' copies and kernels finish first
+    cudaStreamSynchronize(p->stream);
+    free_host_pipeline(p);
+  }
+  const size_t n = (size_t)dp_plan::NSTAGE * chunk;
+  const size_t hb = (size_t)p->d.B * p->d.U, sb = (size_t)p->d.K * p->d.U,
+               xb = (size_t)p->d.K * p->d.B;
+  bool ok = cudaMalloc(&p->hp_H, n * hb * sizeof(float2)) == cudaSuccess &&
+            (sb == 0 || cudaMalloc(&p->hp_S, n * sb * sizeof(float2)) == cudaSuccess) &&
+            (xb == 0 || cudaMalloc(&p->hp_X, n * xb * sizeof(float2)) == cudaSuccess);
+  ok = ok && cudaStreamCreateWithFlags(&p->hp_up, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaStreamCreateWithFlags(&p->hp_down, cudaStreamNonBlocking) == cudaSuccess &&
+       cudaEventCreateWithFlags(&p->hp_start, cudaEventDisableTiming) == cudaSuccess;
+  for (int b = 0; ok && b < dp_plan::NSTAGE; ++b)
+    ok = cudaEventCreateWithFlags(&p->hp_up_done[b], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&p->hp_calc_done[b], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&p->hp_down_done[b], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    free_host_pipeline(p);
+    return DP_ERR_OOM;
+  }
+  p->hp_chunk = chunk;
   return DP_OK;
 }
 
@@ -211,6 +269,7 @@ dp_status dp_plan_destroy(dp_plan_t p) {
   if (!p) return DP_ERR_INVALID_ARG;
   cudaSetDevice(p->device);
   cudaStreamSynchronize(p->stream);
+  free_host_pipeline(p);
   cudaFree(p->d_off);
   cudaFree(p->d_status);
   cudaFree(p->w_G);
@@ -274,39 +333,105 @@ dp_status dp_precode_apply(dp_plan_t p, const void *H, const void *Z, const floa
                                       static_cast<float2 *>(X), p->stream));
 }
 
+namespace {
+
+// Steps a1-a6 for subcarriers [0, n_sc) of the given arrays (a chunk of the
+// plan's subcarriers when n_sc < the plan's), status to `status`
+// [n_sc * nsys], enqueued on the plan's stream.
+cudaError_t precode_range(dp_plan *p, const float2 *h, const float2 *sy, float2 *x, int n_sc,
+                          int *status) {
+  const bool fd = p->d.mode == DP_FDWF;
+  dp::SysDesc sd = make_sys(p, fd, h);
+  sd.n_sc = n_sc;
+  cudaError_t e = cudaSuccess;
+  if (p->has_small) {  // FD-WF clusters with B_c < U: the paper's B_c x B_c form
+    sd.skip_small = 1;
+    e = dp::launch_fd_small(dp::InstDesc{sd, h, sy, x, status, nullptr}, p->bcp, p->stream);
+    if (e != cudaSuccess || p->all_small) return e;
+  }
+  if (p->d.prec != DP_FP32 && dp::pipe_tc_supported(sd, p->UP))
+    return dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
+                              p->stream);
+  if (p->d.prec != DP_FP32)
+    return dp::launch_fused_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
+                               p->stream);
+  if (p->fused_fits)
+    return dp::launch_fused(sd, p->UP, p->maxrows_sys, h, sy, x, status, nullptr, p->stream);
+  // Streaming form: Gram (cluster sum fused for WF/ZF), solve, apply.
+  if (ensure_workspace(p) != DP_OK) return cudaErrorMemoryAllocation;
+  e = dp::launch_gram(sd, p->UP, h, p->w_G, p->stream);
+  if (e == cudaSuccess)
+    e = dp::launch_solve(sd, p->UP, p->w_G, sy, p->w_Z, p->w_scale, status, p->stream);
+  if (e == cudaSuccess) e = dp::launch_apply(sd, p->UP, h, p->w_Z, p->w_scale, x, p->stream);
+  return e;
+}
+
+}  // namespace
+
 dp_status dp_precode(dp_plan_t p, const void *H, const void *S, void *X) {
   if (!p) return DP_ERR_INVALID_ARG;
   if (p->d.n_sc == 0) return DP_OK;
   const bool k0 = p->d.K == 0;
   if (!arg_ok(H, false) || !arg_ok(S, k0) || !arg_ok(X, k0)) return DP_ERR_INVALID_ARG;
   if (dp_status s = set_device(p)) return s;
-  const bool fd = p->d.mode == DP_FDWF;
-  dp::SysDesc sd = make_sys(p, fd, H);
-  const float2 *h = static_cast<const float2 *>(H);
-  const float2 *sy = static_cast<const float2 *>(S);
-  float2 *x = static_cast<float2 *>(X);
-  cudaError_t e = cudaSuccess;
-  if (p->has_small) {  // FD-WF clusters with B_c < U: the paper's B_c x B_c form
-    sd.skip_small = 1;
-    e = dp::launch_fd_small(dp::InstDesc{sd, h, sy, x, p->d_status, nullptr}, p->bcp, p->stream);
-    if (e != cudaSuccess || p->all_small) return cuda_status(e);
+  const cudaError_t e = precode_range(p, static_cast<const float2 *>(H),
+                                      static_cast<const float2 *>(S), static_cast<float2 *>(X),
+                                      p->d.n_sc, p->d_status);
+  return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : cuda_status(e);
+}
+
+dp_status dp_precode_host(dp_plan_t p, const void *H, const void *S, void *X, int chunk_sc) {
+  if (!p) return DP_ERR_INVALID_ARG;
+  const int n_sc = p->d.n_sc;
+  if (n_sc == 0) return DP_OK;
+  const bool k0 = p->d.K == 0;
+  if (!H || (!k0 && (!S || !X))) return DP_ERR_INVALID_ARG;
+  if (dp_status s = set_device(p)) return s;
+  int chunk = chunk_sc > 0 ? chunk_sc : (n_sc + 7) / 8;
+  if (chunk > n_sc) chunk = n_sc;
+  if (dp_status s = ensure_host_pipeline(p, chunk)) return s;
+  const size_t hb = (size_t)p->d.B * p->d.U * sizeof(float2),
+               sb = (size_t)p->d.K * p->d.U * sizeof(float2),
+               xb = (size_t)p->d.K * p->d.B * sizeof(float2);
+  const char *Hh = static_cast<const char *>(H);
+  const char *Sh = static_cast<const char *>(S);
+  char *Xh = static_cast<char *>(X);
+  const size_t stage = (size_t)p->hp_chunk;
+  // uploads start after the work already on the plan's stream (earlier
+  // calls' downloads included: the plan's stream waited for them)
+  cudaError_t e = cudaEventRecord(p->hp_start, p->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hp_up, p->hp_start, 0);
+  const int nchunks = (n_sc + chunk - 1) / chunk;
+  for (int i = 0; i < nchunks && e == cudaSuccess; ++i) {
+    const int b = i % dp_plan::NSTAGE;
+    const int n0 = i * chunk, nc = n_sc - n0 < chunk ? n_sc - n0 : chunk;
+    float2 *dH = p->hp_H + stage * b * (hb / sizeof(float2));
+    float2 *dS = sb ? p->hp_S + stage * b * (sb / sizeof(float2)) : nullptr;
+    float2 *dX = xb ? p->hp_X + stage * b * (xb / sizeof(float2)) : nullptr;
+    // stage b's H and S are free once chunk i - 3 was precoded
+    if (i >= dp_plan::NSTAGE) e = cudaStreamWaitEvent(p->hp_up, p->hp_calc_done[b], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dH, Hh + hb * n0, hb * nc, cudaMemcpyHostToDevice, p->hp_up);
+    if (e == cudaSuccess && sb)
+      e = cudaMemcpyAsync(dS, Sh + sb * n0, sb * nc, cudaMemcpyHostToDevice, p->hp_up);
+    if (e == cudaSuccess) e = cudaEventRecord(p->hp_up_done[b], p->hp_up);
+    // the kernels: after the upload, and once stage b's X went home
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->stream, p->hp_up_done[b], 0);
+    if (e == cudaSuccess && i >= dp_plan::NSTAGE)
+      e = cudaStreamWaitEvent(p->stream, p->hp_down_done[b], 0);
+    if (e == cudaSuccess)
+      e = precode_range(p, dH, dS, dX, nc, p->d_status + (size_t)n0 * p->nsys);
+    if (e == cudaSuccess) e = cudaEventRecord(p->hp_calc_done[b], p->stream);
+    // the download
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->hp_down, p->hp_calc_done[b], 0);
+    if (e == cudaSuccess && xb)
+      e = cudaMemcpyAsync(Xh + xb * n0, dX, xb * nc, cudaMemcpyDeviceToHost, p->hp_down);
+    if (e == cudaSuccess) e = cudaEventRecord(p->hp_down_done[b], p->hp_down);
   }
-  if (p->d.prec != DP_FP32 && dp::pipe_tc_supported(sd, p->UP))
-    return cuda_status(dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, p->d_status,
-                                          nullptr, p->stream));
-  if (p->d.prec != DP_FP32)
-    return cuda_status(dp::launch_fused_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, p->d_status,
-                                           nullptr, p->stream));
-  if (p->fused_fits)
-    return cuda_status(
-        dp::launch_fused(sd, p->UP, p->maxrows_sys, h, sy, x, p->d_status, nullptr, p->stream));
-  // Streaming form: Gram (cluster sum fused for WF/ZF), solve, apply.
-  if (dp_status s = ensure_workspace(p)) return s;
-  e = dp::launch_gram(sd, p->UP, h, p->w_G, p->stream);
-  if (e == cudaSuccess)
-    e = dp::launch_solve(sd, p->UP, p->w_G, sy, p->w_Z, p->w_scale, p->d_status, p->stream);
-  if (e == cudaSuccess) e = dp::launch_apply(sd, p->UP, h, p->w_Z, p->w_scale, x, p->stream);
-  return cuda_status(e);
+  // the call completes on the plan's stream
+  for (int i = nchunks - dp_plan::NSTAGE; i < nchunks && e == cudaSuccess; ++i)
+    if (i >= 0) e = cudaStreamWaitEvent(p->stream, p->hp_down_done[i % dp_plan::NSTAGE], 0);
+  return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : cuda_status(e);
 }
 
 dp_status dp_status_get(dp_plan_t p, int *host_status) {

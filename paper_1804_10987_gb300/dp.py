@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True):
         L.dp_solve.argtypes = [P, P, P, P, P]
         L.dp_precode_apply.argtypes = [P, P, P, P, P]
         L.dp_precode.argtypes = [P, P, P, P]
+        L.dp_precode_host.argtypes = [P, P, P, P, I]
         L.dp_status_get.argtypes = [P, P]
         L.dp_status_string.argtypes = [I]
         L.dp_status_string.restype = ctypes.c_char_p
@@ -137,6 +138,21 @@ def _ptr(t, dtype, shape, name):
         raise TypeError(f"{name} must be a torch tensor")
     if not t.is_cuda:
         raise ValueError(f"{name} must live on a CUDA device")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.device.type != "cpu":
+        raise ValueError(f"{name} must live in host memory")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if tuple(t.shape) != tuple(shape):
@@ -247,6 +263,17 @@ class Plan:
         _check(self._lib.dp_precode(self._h, _ptr(H, torch.complex64, s["H"], "H"),
                                     _ptr(S, torch.complex64, s["S"], "S"),
                                     _ptr(X, torch.complex64, s["X"], "X")), "dp_precode")
+
+    def precode_host(self, H, S, X, chunk: int = 0):
+        """dp_precode_host: H, S, X are host (CPU) tensors -- page-locked ones
+        (``pin_memory()``) let the chunked uploads, kernels and downloads
+        overlap.  Completes on the plan's stream."""
+        import torch
+        s = self.shapes()
+        _check(self._lib.dp_precode_host(self._h, _host_ptr(H, torch.complex64, s["H"], "H"),
+                                         _host_ptr(S, torch.complex64, s["S"], "S"),
+                                         _host_ptr(X, torch.complex64, s["X"], "X"), int(chunk)),
+               "dp_precode_host")
 
     def status_get(self) -> np.ndarray:
         out = np.zeros(max(self.n_sc, 1), np.int32)
