@@ -505,6 +505,17 @@ def our_arm(args):
                "rel_err_max": rel_err_max(X[: w["n_sc"]].cpu().numpy(), Xref)}
         if X_plain is not None:
             cpu["rel_err_max_plain_fp32"] = rel_err_max(X_plain[: w["n_sc"]].cpu().numpy(), Xref)
+        # the same oracle on one host thread, over the slot's first 120 subcarriers
+        import oracle
+        sub, per1 = 120, []
+        t_end = time.perf_counter() + min(3.0, args.cpu_seconds)
+        while not per1 or time.perf_counter() < t_end:
+            t0 = time.perf_counter()
+            oracle.precode(Hs[:sub], Ss[:sub], slot.cluster_sizes, args.mode, rho2=1.0, N0=N0,
+                           Es=1.0, tau=0.125, nthreads=1, outputs=("X",))
+            per1.append(time.perf_counter() - t0)
+        cpu["value_1_thread"] = sub * len(per1) / sum(per1)
+        cpu["sample_1_thread"] = f"{len(per1)} x the slot's first {sub} subcarriers, 1 thread"
 
     plan.close()
     del H, S, X, X_plain

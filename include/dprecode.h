@@ -95,8 +95,14 @@ typedef struct {
   float N0;                  /* noise variance per entry >= 0 (WF, FD) */
   float Es;                  /* symbol energy E|s_u|^2 > 0 (1 for normalized QAM) */
   float tau;                 /* FD-WF tau_c >= 0 (Eq. (16)); ignored otherwise */
-  int refine;                /* 1: one step of iterative refinement of z after a
-                                reduced-precision Gram (FP64 residual); 0: none */
+  int refine;                /* 1 with BF16/FP16: one step of iterative refinement
+                                of z against the reduced-precision Gram -- the
+                                residual r = s - (H H^H + kappa I) z from the exact
+                                FP32 H with FP32 accumulation, z += (G_lp +
+                                kappa I)^{-1} r, then the apply again (U <= 32,
+                                else DP_ERR_UNSUPPORTED); the precoding factor
+                                keeps the low-precision inverse's value;
+                                ignored for DP_FP32; 0: none */
 } dp_plan_desc;
 
 typedef struct dp_plan *dp_plan_t;

@@ -70,6 +70,7 @@ dp::SysDesc make_sys(const dp_plan *p, bool per_cluster, const void *H) {
       break;
   }
   s.tma_ok = (p->d.U % 2 == 0) && (H == nullptr || aligned16(H));
+  s.refine = p->d.refine != 0 && p->d.prec != DP_FP32;
   return s;
 }
 
@@ -189,9 +190,9 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
     return DP_ERR_INVALID_ARG;
   if (d.refine != 0 && d.refine != 1) return DP_ERR_INVALID_ARG;
-  // The tensor-core path covers up to 64 users; refinement is not built.
+  // The tensor-core path covers up to 64 users, its refinement step up to 32.
   if (d.prec != DP_FP32 && !dp::tc_supported(dp::padded_users(d.U))) return DP_ERR_UNSUPPORTED;
-  if (d.refine != 0) return DP_ERR_UNSUPPORTED;
+  if (d.refine && d.prec != DP_FP32 && dp::padded_users(d.U) > 32) return DP_ERR_UNSUPPORTED;
 
   std::vector<int> sizes(d.C);
   if (d.cluster_sizes) {

@@ -66,7 +66,8 @@ dp_status validate(const dp_plan_desc &d, std::vector<int> &off) {
   if (!(d.rho2 > 0.f) || !std::isfinite(d.rho2) || !(d.Es > 0.f) || !std::isfinite(d.Es) ||
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
     return DP_ERR_INVALID_ARG;
-  if (d.refine != 0) return DP_ERR_UNSUPPORTED;
+  if (d.refine != 0 && d.refine != 1) return DP_ERR_INVALID_ARG;
+  if (d.refine && d.prec != DP_FP32 && dp::padded_users(d.U) > 32) return DP_ERR_UNSUPPORTED;
   off.assign(d.C + 1, 0);
   for (int c = 0; c < d.C; ++c) {
     int bc;
@@ -112,6 +113,7 @@ dp::SysDesc sys_of(const Inst &in, const void *H) {
   }
   s.tma_ok = (d.U % 2 == 0) && (H == nullptr || a16(H));
   s.skip_small = in.has_small ? 1 : 0;
+  s.refine = d.refine != 0 && d.prec != DP_FP32;
   return s;
 }
 

@@ -138,6 +138,7 @@ struct SysDesc {
   int tma_ok;       // rows may be fetched with 1-D bulk copies
   int skip_small;   // FD-WF: systems with fewer antennas than users (and at
                     // most 32) are left to the B_c x B_c kernel
+  int refine;       // tensor-core path: one step of iterative refinement of z
 };
 
 // One precoding instance: its systems and its device arrays (H [n_sc][B][U],

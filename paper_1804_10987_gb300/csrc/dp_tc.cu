@@ -52,6 +52,8 @@ struct TcGeo {
                 "half of P and the inverse fit the region");
   // realified users per apply K-block (one 128-byte row of 16-bit entries)
   static constexpr int KBLK = (2 * UP + 63) / 64;
+  // refinement keeps dz [NG][K][UP] (K <= 64) in the region
+  static_assert(LARGE || (size_t)NG * 64 * UP * 8 <= REGION, "dz fits the region");
   static constexpr int MIN_BLOCKS = UP <= 16 ? 3 : 2;  // U > 32: one system, CTA solve
   __device__ static __forceinline__ int p_index(int s, int r, int c) {
     return (s * M2 + r) * PS + (P_PAD ? c : (c ^ (r & 31)));
@@ -79,7 +81,7 @@ __host__ __device__ TcSmem tc_smem_layout(int K) {
   L.Z = take((size_t)T::NG * K * UP * 8 + 16, 16);
   L.scale = take((size_t)(T::NG + NT / 32) * 4, 16);
   L.status = take((size_t)T::NG * 4, 16);
-  L.info = take((size_t)T::NG * 4 * 4, 16);
+  L.info = take((size_t)T::NG * 5 * 4, 16);
   L.bars = take(3 * 8, 8);
   L.tmem = take(4, 4);
   L.total = o + 1024;  // slack to align the dynamic base to 1024 bytes
@@ -168,6 +170,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   int *nr_s = lo_s + NG;                                // antennas of each system
   int *n_s = nr_s + NG;                                 // subcarrier of each system
   int *sk_s = n_s + NG;                                 // system left to another kernel
+                                                        // (then NG refinement flags)
   uint64_t *bar_tma = reinterpret_cast<uint64_t *>(base + L.bars);
   const uint32_t taddr = cx.taddr;
 
@@ -414,7 +417,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   // K-blocks of 64 (one 128-byte swizzled row), accumulated in TMEM.  Split
   // FP16 keeps ~22 bits: A = A_hi + 2^-11 A_lo, z = z_hi + z_lo, D = A_hi z_hi
   // + A_hi z_lo + A_lo (2^-11 z_hi); z is first normalized by a power of two.
-  {
+  auto apply_all = [&]() {
     unsigned char *a_hi = base + L.region;
     unsigned char *a_lo = a_hi + TILE_BYTES;
     unsigned char *b_op = a_hi + 2 * TILE_BYTES;  // hi, lo, hi * 2^-11
@@ -552,7 +555,64 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
       }
     }
     __syncthreads();
+  };
+  apply_all();
+
+  if constexpr (!T::LARGE) {
+    if (d.refine && ok) {
+      // ---- one step of iterative refinement of z ----------------------------
+      // With the exact H in FP32: r = s - (H H^H z0 + kappa z0), where H^H z0
+      // is the apply's X / scale; dz = A_lp^{-1} r with the low-precision
+      // A_lp = G_lp + kappa I kept in shared memory; z1 = z0 + dz; apply again.
+      float2 *Dz = reinterpret_cast<float2 *>(base + L.region);  // [NG][K][UP]
+      int *rf_s = sk_s + NG;                                      // refine system s
+      for (int s = 0; s < nact; ++s) {
+        if (sk_s[s] || st_s[s] != ST_OK) {
+          if (tid == 0) rf_s[s] = 0;
+          continue;
+        }
+        const float inv = 1.f / sc_s[s];
+        const float2 *hs = H + ((size_t)n_s[s] * d.B + lo_s[s]) * U;
+        const float2 *xs = X + (size_t)n_s[s] * K * d.B + lo_s[s];  // written above: plain loads
+        float2 *ss = Ss + s * K * UP;
+        const float2 *zz = Zs + s * K * UP;
+        bool fin = true;
+        for (int e = tid; e < K * UP; e += NT) {
+          const int k = e / UP, u = e - k * UP;
+          if (u >= U) continue;
+          float2 acc = make_float2(0.f, 0.f);
+          for (int b = 0; b < nr_s[s]; ++b)
+            cmac(acc, __ldg(hs + (size_t)b * U + u), xs[(size_t)k * d.B + b]);
+          const float2 z0 = zz[e];
+          float2 r = ss[e];
+          r.x -= acc.x * inv + d.kappa * z0.x;
+          r.y -= acc.y * inv + d.kappa * z0.y;
+          fin = fin && cfinite(r);
+          ss[e] = r;
+        }
+        const int okr = __syncthreads_and(fin);
+        if (tid == 0) rf_s[s] = okr;
+      }
+      __syncthreads();
+      if (warp < nact && rf_s[warp]) {
+        float unused;
+        warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP, Dz + warp * K * UP, UP, d.kappa,
+                       d.rho2_sys, d.Es, U, K, lane, true, unused);
+      }
+      __syncthreads();
+      for (int e = tid; e < NG * K * UP; e += NT) {
+        const int s = e / (K * UP), u = e % UP;
+        if (s < nact && rf_s[s] && u < U) {
+          Zs[e].x += Dz[e].x;
+          Zs[e].y += Dz[e].y;
+        }
+      }
+      fence_proxy_async_smem();
+      __syncthreads();
+      apply_all();
+    }
   }
+
   if (!ok) {
     for (int s = 0; s < nact; ++s) {
       if (sk_s[s]) continue;

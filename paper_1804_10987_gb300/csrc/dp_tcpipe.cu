@@ -756,7 +756,7 @@ cudaError_t launch_pipe_t(const SysDesc &d, const float2 *H, const float2 *S, fl
 }  // namespace
 
 bool pipe_tc_supported(const SysDesc &d, int UP) {
-  return (UP == 8 || UP == 16) && d.tma_ok && d.K >= 1 && d.K <= PP_KMAX;
+  return (UP == 8 || UP == 16) && d.tma_ok && d.K >= 1 && d.K <= PP_KMAX && !d.refine;
 }
 
 cudaError_t launch_pipe_tc(const SysDesc &d, int UP, bool bf16, const float2 *H,

@@ -311,7 +311,7 @@ class Batch:
                               int(d["K"]), MODES[d.get("mode", "wf")],
                               PRECISIONS[d.get("prec", "fp32")], float(d.get("rho2", 1.0)),
                               float(d.get("N0", 0.1)), float(d.get("Es", 1.0)),
-                              float(d.get("tau", 0.125)), 0)
+                              float(d.get("tau", 0.125)), int(d.get("refine", 0)))
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
