@@ -65,7 +65,12 @@ typedef enum {
   DP_ERR_TIMEOUT = 8       /* a bounded on-device wait gave up */
 } dp_status;
 
-typedef enum { DP_ZF = 0, DP_WF = 1, DP_FDWF = 2 } dp_mode;
+/* DP_ZF: kappa = 0.  DP_WF: Thm. 1, computed as PD-WF through the summed
+ * cluster Grams (Sec. III-B).  DP_FDWF: Sec. III-D, Eq. (16).  DP_MRT:
+ * maximum ratio transmission, the fully distributed baseline the paper
+ * compares against (Sec. I, Sec. III-E): x = scale H^H s with scale = rho /
+ * sqrt(Es tr(G)) -- no inverse; dp_solve returns Z = S. */
+typedef enum { DP_ZF = 0, DP_WF = 1, DP_FDWF = 2, DP_MRT = 3 } dp_mode;
 
 /* Arithmetic of the path (Sec. III-B).  DP_FP32: every step in FP32 on the
  * SIMT cores.  DP_BF16 / DP_FP16: the Gram contraction G_c = H_c H_c^H on the

@@ -24,8 +24,8 @@ _HDR = os.path.join(_HERE, "dp_oracle.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
-ZF, WF, FDWF = 0, 1, 2
-MODES = {"zf": ZF, "wf": WF, "fdwf": FDWF}
+ZF, WF, FDWF, MRT = 0, 1, 2, 3
+MODES = {"zf": ZF, "wf": WF, "fdwf": FDWF, "mrt": MRT}
 FORM_PAPER, FORM_UXU, FORM_BCXBC = 0, 1, 2
 OK, NOT_PD, NONFINITE, BAD_ARG = 0, 1, 2, 3
 

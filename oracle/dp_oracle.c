@@ -166,6 +166,34 @@ static int solve_u_form(const orc_desc *d, const orc_cplx *Hn, const orc_cplx *S
   return ORC_OK;
 }
 
+/* MRT (Sec. I; the fully distributed baseline of Sec. III-E): P = H^H / beta
+ * with E||x||^2 = rho^2, i.e. t = tr(H H^H) = tr(G), scale = rho / sqrt(Es t);
+ * z = s.  td: ||H||_F^2 summed over the entries of H. */
+static int solve_mrt(const orc_desc *d, const orc_cplx *Hn, const orc_cplx *Sn,
+                     const orc_cplx *G, orc_cplx *Xn, orc_cplx *Zc, double *scale_out,
+                     double *t_out, double *td_out) {
+  int U = d->U, K = d->K, B = d->B;
+  double t = 0.0, td = 0.0;
+  for (int i = 0; i < U; ++i) t += RE(G[i * U + i]);
+  for (size_t i = 0; i < (size_t)B * U; ++i) td += RE(Hn[i]) * RE(Hn[i]) + IM(Hn[i]) * IM(Hn[i]);
+  if (!(t > 0.0) || !isfinite(t)) return ORC_NOT_PD;
+  double scale = sqrt(d->rho2 / (d->Es * t));
+  for (int k = 0; k < K; ++k) {
+    const orc_cplx *s = Sn + (size_t)k * U;
+    if (Zc)
+      for (int i = 0; i < U; ++i) Zc[(size_t)k * U + i] = s[i];
+    for (int b = 0; b < B; ++b) {
+      orc_cplx acc = 0;
+      for (int u = 0; u < U; ++u) acc += conj(Hn[(size_t)b * U + u]) * s[u];
+      Xn[(size_t)k * B + b] = scale * acc;
+    }
+  }
+  *scale_out = scale;
+  *t_out = t;
+  *td_out = td;
+  return ORC_OK;
+}
+
 /* FD-WF with B_c < U (Sec. III-D, first case):
  * Q_c = (H_c^H H_c + kappa_c I_{B_c})^{-1} H_c^H, t = tr(Q_c^H Q_c),
  * x_c = sqrt(rho_c^2 / (t Es)) Q_c s.  Q[a][u] for antenna a, user u. */
@@ -252,7 +280,10 @@ static void *worker(void *arg) {
 
     for (int g = 0; g < nsys && st == ORC_OK; ++g) {
       double sc_v = 0, t_v = 0, td_v = 0;
-      if (d->mode != ORC_FDWF) {
+      if (d->mode == ORC_MRT) {
+        orc_cplx *Zn = jb->Z ? jb->Z + (size_t)n * K * U : NULL;
+        st = solve_mrt(d, Hn, Sn, Gs, Xtmp, Zn, &sc_v, &t_v, &td_v);
+      } else if (d->mode != ORC_FDWF) {
         double kappa = (d->mode == ORC_WF) ? d->U * d->N0 / d->rho2 : 0.0;
         orc_cplx *Zn = jb->Z ? jb->Z + (size_t)n * K * U : NULL;
         st = solve_u_form(d, Hn, Sn, 0, B, Gs, kappa, d->rho2, A, L, T, zb, Xtmp, Zn,
@@ -319,7 +350,8 @@ int orc_precode(const orc_desc *d, const orc_cplx *H, const orc_cplx *S,
   if (!d || !H || !S || d->U < 1 || d->B < 1 || d->C < 1 || d->n_sc < 0 || d->K < 0 ||
       !d->cluster_sizes || !(d->rho2 > 0) || !(d->Es > 0) || d->N0 < 0 || d->tau < 0)
     return ORC_BAD_ARG;
-  if (d->mode != ORC_ZF && d->mode != ORC_WF && d->mode != ORC_FDWF) return ORC_BAD_ARG;
+  if (d->mode != ORC_ZF && d->mode != ORC_WF && d->mode != ORC_FDWF && d->mode != ORC_MRT)
+    return ORC_BAD_ARG;
   int *off = (int *)malloc(sizeof(int) * (d->C + 1));
   off[0] = 0;
   for (int c = 0; c < d->C; ++c) {

@@ -21,10 +21,11 @@
  *   scale WF/ZF [n_sc],       FD [n_sc][C]         scale = 1 / beta
  *   t     same shape as scale: the tr(Q^H Q) the scale was formed from
  *         (Lemma 1 in the U x U form; the definition ||Q_c||_F^2 in the FD
- *         B_c x B_c form)
+ *         B_c x B_c form; tr(G) for MRT)
  *   t_alt same shape: the other formula for the same quantity (the direct
  *         tr(A^{-1} G A^{-1}) of Appendix B, resp. Lemma 1 on the B_c x B_c
- *         inverse), kept for the pins that the two agree
+ *         inverse, resp. ||H||_F^2 summed over H for MRT), kept for the pins
+ *         that the two agree
  */
 #ifndef DP_ORACLE_H
 #define DP_ORACLE_H
@@ -37,7 +38,10 @@ extern "C" {
 
 typedef double _Complex orc_cplx;
 
-enum { ORC_ZF = 0, ORC_WF = 1, ORC_FDWF = 2 };
+/* ORC_MRT: maximum ratio transmission, the fully distributed baseline the
+ * paper compares against (Sec. I, Sec. III-E): x = scale H^H s with
+ * scale = rho / sqrt(Es tr(H^H H)); z = s. */
+enum { ORC_ZF = 0, ORC_WF = 1, ORC_FDWF = 2, ORC_MRT = 3 };
 enum { ORC_OK = 0, ORC_NOT_PD = 1, ORC_NONFINITE = 2, ORC_BAD_ARG = 3 };
 /* FD-WF form selection: the rule of Sec. III-D (B_c < U uses the B_c x B_c
  * inverse, otherwise the U x U one), or one form forced for the pin that the
@@ -48,7 +52,7 @@ typedef struct {
   int U, B, C;
   const int *cluster_sizes; /* C entries, each >= 1, summing to B */
   int n_sc, K;
-  int mode;                 /* ORC_ZF, ORC_WF, ORC_FDWF */
+  int mode;                 /* ORC_ZF, ORC_WF, ORC_FDWF, ORC_MRT */
   double rho2, N0, Es, tau; /* tau: FD-WF regularization factor tau_c */
   int fd_form;              /* ORC_FORM_* */
 } orc_desc;

@@ -57,6 +57,7 @@ dp::SysDesc make_sys(const dp_plan *p, bool per_cluster, const void *H) {
   const double U = p->d.U, N0 = p->d.N0, rho2 = p->d.rho2, C = p->d.C;
   switch (p->d.mode) {
     case DP_ZF:
+    case DP_MRT:
       s.kappa = 0.f;
       s.rho2_sys = p->d.rho2;
       break;
@@ -71,6 +72,7 @@ dp::SysDesc make_sys(const dp_plan *p, bool per_cluster, const void *H) {
   }
   s.tma_ok = (p->d.U % 2 == 0) && (H == nullptr || aligned16(H));
   s.refine = p->d.refine != 0 && p->d.prec != DP_FP32;
+  s.mrt = p->d.mode == DP_MRT;
   return s;
 }
 
@@ -184,7 +186,8 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
   if (d.U < 1 || d.U > 64 || d.B < 1 || d.B > 4096 || d.C < 1 || d.C > d.B || d.n_sc < 0 ||
       d.K < 0 || d.K > 64)
     return DP_ERR_INVALID_ARG;
-  if (d.mode != DP_ZF && d.mode != DP_WF && d.mode != DP_FDWF) return DP_ERR_INVALID_ARG;
+  if (d.mode != DP_ZF && d.mode != DP_WF && d.mode != DP_FDWF && d.mode != DP_MRT)
+    return DP_ERR_INVALID_ARG;
   if (d.prec != DP_FP32 && d.prec != DP_BF16 && d.prec != DP_FP16) return DP_ERR_INVALID_ARG;
   if (!(d.rho2 > 0.f) || !std::isfinite(d.rho2) || !(d.Es > 0.f) || !std::isfinite(d.Es) ||
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))

@@ -61,7 +61,8 @@ dp_status validate(const dp_plan_desc &d, std::vector<int> &off) {
   if (d.U < 1 || d.U > 64 || d.B < 1 || d.B > 4096 || d.C < 1 || d.C > d.B || d.n_sc < 0 ||
       d.K < 0 || d.K > 64)
     return DP_ERR_INVALID_ARG;
-  if (d.mode != DP_ZF && d.mode != DP_WF && d.mode != DP_FDWF) return DP_ERR_INVALID_ARG;
+  if (d.mode != DP_ZF && d.mode != DP_WF && d.mode != DP_FDWF && d.mode != DP_MRT)
+    return DP_ERR_INVALID_ARG;
   if (d.prec != DP_FP32 && d.prec != DP_BF16 && d.prec != DP_FP16) return DP_ERR_INVALID_ARG;
   if (!(d.rho2 > 0.f) || !std::isfinite(d.rho2) || !(d.Es > 0.f) || !std::isfinite(d.Es) ||
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
@@ -101,7 +102,7 @@ dp::SysDesc sys_of(const Inst &in, const void *H) {
   s.off = in.d_off;
   s.Es = d.Es;
   const double U = d.U, N0 = d.N0, rho2 = d.rho2, C = d.C;
-  if (d.mode == DP_ZF) {
+  if (d.mode == DP_ZF || d.mode == DP_MRT) {
     s.kappa = 0.f;
     s.rho2_sys = d.rho2;
   } else if (d.mode == DP_WF) {
@@ -114,6 +115,7 @@ dp::SysDesc sys_of(const Inst &in, const void *H) {
   s.tma_ok = (d.U % 2 == 0) && (H == nullptr || a16(H));
   s.skip_small = in.has_small ? 1 : 0;
   s.refine = d.refine != 0 && d.prec != DP_FP32;
+  s.mrt = d.mode == DP_MRT;
   return s;
 }
 

@@ -163,6 +163,17 @@ __device__ __forceinline__ float cta_sum(float v, float *red, int tid) {
   return s;
 }
 
+// MRT's precoding factor t = tr(G) over a CTA (G [UP][UP] in shared memory),
+// and z = s (Ss, Zs [K][UP]).
+template <int UP>
+__device__ float cta_mrt(const float2 *G, const float2 *Ss, float2 *Zs, int U, int K, float *red,
+                         int tid) {
+  float v = 0.f;
+  for (int i = tid; i < U; i += NT) v += G[i * UP + i].x;
+  for (int e = tid; e < K * UP; e += NT) Zs[e] = Ss[e];
+  return cta_sum(v, red, tid);
+}
+
 // ------------------------------------------------- CTA-wide inversion ------
 // In-place Gauss-Jordan inversion of the Hermitian positive definite A
 // [UP][UP] (leading U x U block), no pivoting: for a positive definite matrix
@@ -376,15 +387,16 @@ __device__ __forceinline__ int split_solve(float2 (&row)[UP / 2], const float2 *
                                            const float2 *Ss, float2 *zout, int ldz, float kappa,
                                            float rho2, float Es, int U, int K, int sl,
                                            bool finite_in, bool store, float &scale,
-                                           float &zmax) {
+                                           float &zmax, bool mrt = false) {
   constexpr int HALF = UP / 2, SEG = 2 * UP;
   static_assert(SEG <= 32, "a system fits a warp");
   const int i = sl % UP, h = sl / UP;
   int st = finite_in ? ST_OK : ST_NONFINITE;
   bool bad = false;
+  // MRT (kappa = 0, no inverse): t = tr(G), z = s; row keeps G
 #pragma unroll
   for (int p = 0; p < UP; ++p) {
-    if (p >= U) break;
+    if (p >= U || mrt) break;
     const int hp = p / HALF, pc = p % HALF;
     const float piv = __shfl_sync(FULL, row[pc].x, p + hp * UP, SEG);
     bad = bad || !(piv > 0.f) || !isfinite(piv);
@@ -423,8 +435,8 @@ __device__ __forceinline__ int split_solve(float2 (&row)[UP / 2], const float2 *
       fr = 0.f;
     }
     const float tr = seg_sum<SEG>(dg), fro = seg_sum<SEG>(fr);
-    float t = tr - kappa * fro;
-    const bool need = kappa * fro > kLemmaMaxRatio * tr;
+    float t = mrt ? tr : tr - kappa * fro;
+    const bool need = !mrt && kappa * fro > kLemmaMaxRatio * tr;
     if (__any_sync(FULL, need && st == ST_OK)) {
       // (T G)_ij from both halves of row i of T, one column j at a time
       float part = 0.f;
@@ -457,7 +469,9 @@ __device__ __forceinline__ int split_solve(float2 (&row)[UP / 2], const float2 *
   float zm = 0.f;
   for (int k = 0; k < K; ++k) {
     float2 acc = make_float2(0.f, 0.f);
-    if (st == ST_OK) {
+    if (st == ST_OK && mrt) {
+      if (h == 0) acc = Ss[k * UP + i];  // the partner adds zero
+    } else if (st == ST_OK) {
 #pragma unroll
       for (int jj = 0; jj < HALF; ++jj) cmac(acc, row[jj], Ss[k * UP + h * HALF + jj]);
     }
@@ -511,7 +525,7 @@ __device__ __forceinline__ bool warp_gj_inverse(float2 (&row)[UP], int lane, int
 template <int UP>
 __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int ldz, float kappa,
                           float rho2, float Es, int U, int K, int lane, bool finite_in,
-                          float &scale) {
+                          float &scale, bool mrt = false) {
   if constexpr (2 * UP <= 32) {  // split rows over 2 UP lanes
     constexpr int HALF = UP / 2, SEG = 2 * UP;
     const int sl = lane % SEG, i = sl % UP, h = sl / UP;
@@ -524,7 +538,7 @@ __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int 
     }
     float zm;
     return split_solve<UP>(row, Gs, Ss, zout, ldz, kappa, rho2, Es, U, K, sl, finite_in,
-                           lane < SEG, scale, zm);
+                           lane < SEG, scale, zm, mrt);
   }
   float2 row[UP];
 #pragma unroll
@@ -533,7 +547,7 @@ __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int 
     if (j == lane) row[j].x += kappa;
   }
   int st = finite_in ? ST_OK : ST_NONFINITE;
-  if (st == ST_OK && !warp_gj_inverse<UP>(row, lane, U)) st = ST_NOT_PD;
+  if (st == ST_OK && !mrt && !warp_gj_inverse<UP>(row, lane, U)) st = ST_NOT_PD;
   float sc = 0.f;
   if (st == ST_OK) {
     // Lemma 1: t = tr(T) - kappa ||T||_F^2.  When kappa ||T||_F^2 / tr(T) is
@@ -550,8 +564,8 @@ __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int 
       fr = 0.f;
     }
     const float tr = warp_sum(dg), fro = warp_sum(fr);
-    float t = tr - kappa * fro;
-    if (kappa * fro > kLemmaMaxRatio * tr) {
+    float t = mrt ? tr : tr - kappa * fro;  // MRT: row holds G, t = tr(G)
+    if (!mrt && kappa * fro > kLemmaMaxRatio * tr) {
       // the cancelling case: lane i forms (T G)_ij = sum_k T_ik G_kj one
       // column j at a time (runtime loop: few live registers)
       float part = 0.f;
@@ -574,7 +588,9 @@ __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int 
   }
   for (int k = 0; k < K; ++k) {
     float2 acc = make_float2(0.f, 0.f);
-    if (st == ST_OK) {
+    if (st == ST_OK && mrt) {
+      acc = Ss[k * UP + (lane < UP ? lane : 0)];  // z = s
+    } else if (st == ST_OK) {
 #pragma unroll
       for (int j = 0; j < UP; ++j) cmac(acc, row[j], Ss[k * UP + j]);
     }

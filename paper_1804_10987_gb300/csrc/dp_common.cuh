@@ -139,6 +139,7 @@ struct SysDesc {
   int skip_small;   // FD-WF: systems with fewer antennas than users (and at
                     // most 32) are left to the B_c x B_c kernel
   int refine;       // tensor-core path: one step of iterative refinement of z
+  int mrt;          // maximum ratio transmission: no inverse, z = s, t = tr(G)
 };
 
 // One precoding instance: its systems and its device arrays (H [n_sc][B][U],

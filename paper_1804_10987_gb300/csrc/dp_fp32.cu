@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(NT) k_solve_warp(SysDesc d, const float2 *__re
 
   float sc = 0.f;
   const int st = warp_solve<UP>(Gw, Sw, Z + (size_t)sys * K * U, U, d.kappa, d.rho2_sys, d.Es, U,
-                                K, lane, fin, sc);
+                                K, lane, fin, sc, d.mrt != 0);
   if (lane == 0) {
     scale[sys] = sc;
     report(status, sys, st);
@@ -190,13 +190,19 @@ __global__ void __launch_bounds__(NT) k_solve_cta(SysDesc d, const float2 *__res
   fin = load_symbols<UP>(S + (size_t)n * K * U, Ss, U, K, tid) && fin;
   int st = fin ? ST_OK : ST_NONFINITE;
   float sc = 0.f;
-  if (st == ST_OK) st = cta_gj_inverse<UP>(A, U, tid);
-  if (st == ST_OK) {
-    const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
+  if (st == ST_OK && d.mrt) {  // MRT: t = tr(G), z = s
+    const float t = cta_mrt<UP>(G, Ss, Zs, U, K, red, tid);
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
     else sc = sqrtf(d.rho2_sys / (d.Es * t));
+  } else {
+    if (st == ST_OK) st = cta_gj_inverse<UP>(A, U, tid);
+    if (st == ST_OK) {
+      const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
+      if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
+      else sc = sqrtf(d.rho2_sys / (d.Es * t));
+    }
   }
-  if (st == ST_OK) cta_whiten<UP>(A, Ss, Zs, U, K, tid);
+  if (st == ST_OK && !d.mrt) cta_whiten<UP>(A, Ss, Zs, U, K, tid);
   __syncthreads();
   float2 *zdst = Z + (size_t)sys * K * U;
   for (int e = tid; e < K * U; e += NT) {
@@ -347,15 +353,21 @@ __device__ bool fused_system(const InstDesc &in, int sys, unsigned char *smem_ra
 
   // a3 + a4: inverse and precoding factor
   float sc = 0.f;
-  if (st == ST_OK) st = cta_gj_inverse<UP>(A, U, tid);
-  if (st == ST_OK) {
-    const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
+  if (st == ST_OK && d.mrt) {  // MRT: t = tr(G), z = s
+    const float t = cta_mrt<UP>(G, Ss, Zs, U, K, red, tid);
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
     else sc = sqrtf(d.rho2_sys / (d.Es * t));
+  } else {
+    if (st == ST_OK) st = cta_gj_inverse<UP>(A, U, tid);
+    if (st == ST_OK) {
+      const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
+      if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
+      else sc = sqrtf(d.rho2_sys / (d.Es * t));
+    }
   }
   // a5 + a6: whiten, then x = scale H^H z over the resident antenna block
   if (st == ST_OK) {
-    cta_whiten<UP>(A, Ss, Zs, U, K, tid);
+    if (!d.mrt) cta_whiten<UP>(A, Ss, Zs, U, K, tid);
     __syncthreads();
     apply_rows<UP, 7>(Hs, nrows, Zs, K, sc, Xn, d.B, lo, tid);
   } else {

@@ -56,7 +56,7 @@ extern "C" dp_status dp_precode_noalloc(const dp_plan_desc *desc, dp_stream_t st
   if (d.U < 1 || d.U > 64 || d.B < 1 || d.B > 4096 || d.C < 1 || d.C > d.B || d.n_sc < 0 ||
       d.K < 0 || d.K > 64)
     return DP_ERR_INVALID_ARG;
-  if (d.mode != DP_ZF && d.mode != DP_WF && d.mode != DP_FDWF) return DP_ERR_INVALID_ARG;
+  if (d.mode != DP_ZF && d.mode != DP_WF && d.mode != DP_FDWF && d.mode != DP_MRT) return DP_ERR_INVALID_ARG;
   if (d.prec != DP_FP32 && d.prec != DP_BF16 && d.prec != DP_FP16) return DP_ERR_INVALID_ARG;
   if (!(d.rho2 > 0.f) || !std::isfinite(d.rho2) || !(d.Es > 0.f) || !std::isfinite(d.Es) ||
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau) ||
@@ -127,7 +127,7 @@ extern "C" dp_status dp_precode_noalloc(const dp_plan_desc *desc, dp_stream_t st
   sd.off = w_off;
   sd.Es = d.Es;
   const double U = d.U, N0 = d.N0, rho2 = d.rho2, C = d.C;
-  if (d.mode == DP_ZF) {
+  if (d.mode == DP_ZF || d.mode == DP_MRT) {
     sd.kappa = 0.f;
     sd.rho2_sys = d.rho2;
   } else if (d.mode == DP_WF) {
@@ -138,6 +138,7 @@ extern "C" dp_status dp_precode_noalloc(const dp_plan_desc *desc, dp_stream_t st
     sd.rho2_sys = (float)(rho2 / C);
   }
   sd.tma_ok = (d.U % 2 == 0) && a16(H);
+  sd.mrt = d.mode == DP_MRT;
   const int UP = dp::padded_users(d.U);
   const float2 *h = static_cast<const float2 *>(H);
   if (e == cudaSuccess) e = dp::launch_gram(sd, UP, h, w_G, st);

@@ -380,13 +380,19 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
     int st = (nact > 0) ? st_s[0] : ST_OK;
     float sc = 0.f;
     if (nact > 0 && !sk_s[0]) {
-      if (st == ST_OK) st = cta_gj_inverse<UP>(Aw, U, tid);
-      if (st == ST_OK) {
-        const float t = cta_trace_tgt<UP>(Aw, Gs, d.kappa, U, sc_s + NG, tid);
+      if (st == ST_OK && d.mrt) {  // MRT: t = tr(G), z = s
+        const float t = cta_mrt<UP>(Gs, Ss, Zs, U, K, sc_s + NG, tid);
         if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
         else sc = sqrtf(d.rho2_sys / (d.Es * t));
+      } else {
+        if (st == ST_OK) st = cta_gj_inverse<UP>(Aw, U, tid);
+        if (st == ST_OK) {
+          const float t = cta_trace_tgt<UP>(Aw, Gs, d.kappa, U, sc_s + NG, tid);
+          if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
+          else sc = sqrtf(d.rho2_sys / (d.Es * t));
+        }
+        if (st == ST_OK) cta_whiten<UP>(Aw, Ss, Zs, U, K, tid);
       }
-      if (st == ST_OK) cta_whiten<UP>(Aw, Ss, Zs, U, K, tid);
     }
     __syncthreads();
     if (tid == 0 && nact > 0) {
@@ -399,7 +405,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
       float sc = 0.f;
       const int st = warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP, Zs + warp * K * UP, UP,
                                     d.kappa, d.rho2_sys, d.Es, U, K, lane, st_s[warp] == ST_OK,
-                                    sc);
+                                    sc, d.mrt != 0);
       if (lane == 0) {
         st_s[warp] = st;
         sc_s[warp] = sc;
@@ -559,7 +565,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   apply_all();
 
   if constexpr (!T::LARGE) {
-    if (d.refine && ok) {
+    if (d.refine && !d.mrt && ok) {
       // ---- one step of iterative refinement of z ----------------------------
       // With the exact H in FP32: r = s - (H H^H z0 + kappa z0), where H^H z0
       // is the apply's X / scale; dz = A_lp^{-1} r with the low-precision

@@ -636,7 +636,7 @@ __device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, 
     const bool finite_in = seg_all<SEG>(fin_s && fin_g, lane);
     float sc = 0.f, zm = 0.f;
     const int st = split_solve<UP>(row, Gw, Sz, Sz, UP, kappa, d.rho2_sys, d.Es, U, K, sl,
-                                   finite_in, true, sc, zm);
+                                   finite_in, true, sc, zm, d.mrt != 0);
     int zexp = 0;
     if (zm > 0.f) frexpf(zm, &zexp);
     if (sl == 0) {

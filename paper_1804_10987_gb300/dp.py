@@ -21,7 +21,7 @@ import numpy as np
 from . import build as _build
 
 OK, INVALID_ARG, PARTITION, UNSUPPORTED, OOM, CUDA, NOT_PD, NONFINITE, TIMEOUT = range(9)
-MODES = {"zf": 0, "wf": 1, "fdwf": 2}
+MODES = {"zf": 0, "wf": 1, "fdwf": 2, "mrt": 3}
 PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
 
 _lock = threading.Lock()

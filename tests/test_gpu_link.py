@@ -7,7 +7,8 @@ precoder) and slices to the constellation.  Two checks:
   the FP64 oracle's outputs on the same channel, symbols and noise;
 * the paper's qualitative ordering: WF (= PD-WF) has the lowest MSE, ZF is
   close to it at high SNR when B >> U, FD-WF with clusters of B_c = 32 >= U
-  stays close to it, and every precoder's MSE falls with the SNR.
+  stays close to it, MRT falls further behind as the SNR grows, and every
+  precoder's MSE falls with the SNR.
 """
 import numpy as np
 import pytest
@@ -46,7 +47,7 @@ def problem(snr, mode="wf", tau=0.125):
 @pytest.mark.parametrize("snr", SNRS)
 @pytest.mark.parametrize("mode,tau,prec", [("wf", 0.125, "fp32"), ("wf", 0.125, "fp16"),
                                            ("zf", 0.125, "fp32"), ("fdwf", 0.125, "fp16"),
-                                           ("fdwf", 1.0, "fp32")])
+                                           ("fdwf", 1.0, "fp32"), ("mrt", 0.125, "fp16")])
 def test_link_metrics_match_oracle(snr, mode, tau, prec):
     p = problem(snr, mode, tau)
     Xg, st = gpu_precode(p, mode, tau, prec=prec)
@@ -61,7 +62,8 @@ def test_link_metrics_match_oracle(snr, mode, tau, prec):
 def test_link_ordering_of_the_precoders():
     res = {}
     for snr in SNRS:
-        for mode, tau in (("wf", 0.125), ("zf", 0.125), ("fdwf", 0.125), ("fdwf", 1.0)):
+        for mode, tau in (("wf", 0.125), ("zf", 0.125), ("fdwf", 0.125), ("fdwf", 1.0),
+                          ("mrt", 0.125)):
             p = problem(snr, mode, tau)
             Xg, _ = gpu_precode(p, mode, tau)
             res[(mode, tau, snr)] = link(p, Xg, 11)[0]
@@ -69,13 +71,17 @@ def test_link_ordering_of_the_precoders():
     for snr in SNRS:
         wf = res[("wf", 0.125, snr)]
         # WF minimizes the MSE; sampling noise allows a 2 % margin
-        for other in (("zf", 0.125), ("fdwf", 0.125), ("fdwf", 1.0)):
+        for other in (("zf", 0.125), ("fdwf", 0.125), ("fdwf", 1.0), ("mrt", 0.125)):
             assert wf <= res[other + (snr,)] * 1.02, (snr, other, wf, res[other + (snr,)])
         # FD-WF with B_c = 32 >= U = 16 stays close to WF
         assert res[("fdwf", 0.125, snr)] <= 1.5 * wf, (snr, res[("fdwf", 0.125, snr)], wf)
     # with B/U = 16 ZF is within a few percent of WF at high SNR, and every
     # precoder's MSE falls with the SNR
     assert res[("zf", 0.125, 20.0)] <= 1.05 * res[("wf", 0.125, 20.0)]
+    # MRT is interference-limited (Sec. I): its gap to WF grows with the SNR
+    # (about 1.27x at 20 dB with B/U = 16)
+    mrt_gap = [res[("mrt", 0.125, s)] / res[("wf", 0.125, s)] for s in SNRS]
+    assert mrt_gap[0] <= mrt_gap[1] <= mrt_gap[2] and mrt_gap[2] >= 1.1, mrt_gap
     for key in (("wf", 0.125), ("zf", 0.125), ("fdwf", 0.125), ("fdwf", 1.0)):
         seq = [res[key + (s,)] for s in SNRS]
         assert seq[0] > seq[1] > seq[2], (key, seq)

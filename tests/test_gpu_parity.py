@@ -207,3 +207,42 @@ def test_fd_small_clusters(U, cs, n_sc, K, snr, prec):
     err = rel_err_per_sc(Xg, ref["X"])
     tol = TOL_FP32 if prec == "fp32" else 1e-3
     assert err.max() <= tol, err.max()
+
+
+# --- MRT: the fully distributed baseline (no inverse; t = tr(G)) ------------------
+
+@pytest.mark.parametrize("U,cs,n_sc,K,prec", [
+    (16, [32] * 8, 300, 14, "fp32"),     # FP32 fused kernel
+    (16, [32] * 8, 300, 14, "fp16"),     # warp-specialized tensor-core kernel
+    (24, [100, 200], 5, 7, "bf16"),      # tensor-core group kernel, warp solve
+    (48, [128, 128, 256], 3, 14, "fp32"),  # FP32 fused kernel, CTA solve
+    (48, [128, 128, 256], 3, 14, "fp16"),  # tensor-core group kernel, U > 32
+    (64, [1024], 1, 14, "fp32"),         # streaming form
+])
+def test_mrt(U, cs, n_sc, K, prec):
+    p = synth.make_problem(U, sum(cs), len(cs), n_sc, K, 16, 10.0, seed=6000 + U + n_sc,
+                           cluster_sizes=cs)
+    Xg, st = gpu_precode(p, "mrt", prec=prec)
+    ref = oracle_of(p, "mrt")
+    assert np.array_equal(st, ref["status"]) and (st == 0).all()
+    err = rel_err_per_sc(Xg, ref["X"])
+    assert err.max() <= (TOL_FP32 if prec == "fp32" else 1e-3), err.max()
+
+
+def test_mrt_split_steps():
+    """dp_solve returns Z = S and the MRT scale; the apply gives X."""
+    import torch
+    p = c1()
+    ref = oracle_of(p, "mrt")
+    pl = plan_of(p, "mrt")
+    H, S = to_dev(p.H), to_dev(p.S)
+    G, Z, sc, X = (pl.empty(k) for k in ("G", "Z", "scale", "X"))
+    Gloc = pl.empty("Gloc")
+    pl.gram_local(H, Gloc)
+    pl.gram_reduce(Gloc, G)
+    pl.solve(G, S, Z, sc)
+    pl.precode_apply(H, Z, sc, X)
+    torch.cuda.synchronize()
+    assert torch.equal(Z, S)
+    np.testing.assert_allclose(sc.cpu().numpy(), ref["scale"], rtol=1e-5)
+    assert rel_err_per_sc(X.cpu().numpy(), ref["X"]).max() < TOL_FP32

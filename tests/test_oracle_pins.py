@@ -193,7 +193,7 @@ def test_fd_single_cluster_tau_equals_wf_at_scaled_noise():
 
 # --- (iv) power constraint -----------------------------------------------------------
 
-@pytest.mark.parametrize("mode", ["wf", "zf", "fdwf"])
+@pytest.mark.parametrize("mode", ["wf", "zf", "fdwf", "mrt"])
 def test_power_constraint_exact(mode):
     U, cs = 4, [5, 3, 8]
     H, _ = random_problem(12, 3, sum(cs), U, 1)
@@ -369,3 +369,40 @@ def test_rejects_bad_partition():
     H, S = random_problem(24, 1, 8, 2, 1)
     with pytest.raises(ValueError):
         oracle.precode(H, S, [4, 3], "wf")
+
+
+# --- MRT (the fully distributed baseline of Sec. III-E) ----------------------------
+
+def test_mrt_is_the_scaled_conjugate_channel():
+    """P = Hm^H rho / (sqrt(Es) ||Hm||_F), straight from numpy; t = tr(G)
+    equals ||H||_F^2 summed over the entries."""
+    cs = [3, 6]
+    H, _ = random_problem(40, 4, sum(cs), 5, 1)
+    P, out = precoder_matrix(H, cs, "mrt", rho2=1.7, Es=1.0)
+    for n in range(4):
+        Hm = H[n].T
+        want = Hm.conj().T * np.sqrt(1.7 / np.linalg.norm(Hm) ** 2)
+        assert np.abs(P[n] - want).max() < 1e-12
+        assert abs(out["t"][n] - out["t_alt"][n]) < 1e-12 * out["t"][n]
+        assert abs(out["t"][n] - np.linalg.norm(Hm) ** 2) < 1e-12 * out["t"][n]
+    assert (out["Z"] == np.broadcast_to(np.eye(5), out["Z"].shape)).all()  # z = s
+
+
+def test_single_user_mrt_wf_and_zf_coincide():
+    """For U = 1 every linear precoder is the normalized conjugate channel."""
+    H, _ = random_problem(41, 3, 7, 1, 1)
+    Pm, _ = precoder_matrix(H, [7], "mrt")
+    Pw, _ = precoder_matrix(H, [7], "wf", N0=0.3)
+    Pz, _ = precoder_matrix(H, [7], "zf")
+    assert np.abs(Pm - Pw).max() < 1e-12 and np.abs(Pm - Pz).max() < 1e-12
+
+
+def test_wf_tends_to_mrt_as_noise_grows():
+    """kappa -> infinity: (G + kappa I)^{-1} -> I / kappa, so the normalized
+    WF precoder tends to MRT (relative gap O(||G|| / kappa))."""
+    cs = [4, 4]
+    H, _ = random_problem(42, 2, sum(cs), 3, 1)
+    Pm, _ = precoder_matrix(H, cs, "mrt")
+    for N0, tol in ((1e3, 1e-2), (1e6, 1e-5)):
+        Pw, _ = precoder_matrix(H, cs, "wf", N0=N0)
+        assert np.abs(Pw - Pm).max() / np.abs(Pm).max() < tol
