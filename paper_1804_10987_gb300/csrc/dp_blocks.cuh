@@ -207,6 +207,84 @@ __device__ int cta_gj_inverse(float2 *A, int U, int tid) {
   return ST_OK;
 }
 
+// The same Gauss-Jordan with A held in registers: thread (bi, bj) of a 16 x 16
+// grid (NT = 256) owns the RB x RB block of rows bi RB + r and columns
+// bj RB + c (RB = ceil(UP / 16)).  Before pivot p the owners publish row p
+// and column p into rc [2][2][UP] (double-buffered by pivot parity: one CTA
+// barrier per pivot).  The arithmetic of every element is that of
+// cta_gj_inverse, so the results are identical.  A is read at entry and
+// holds A^{-1} at exit; the caller has synced after writing A.
+template <int UP>
+__device__ int cta_gj_inverse_reg(float2 *A, int U, int tid, float2 *rc) {
+  static_assert(NT == 256, "a 16 x 16 thread grid");
+  constexpr int RB = (UP + 15) / 16;
+  const int bi = tid >> 4, bj = tid & 15;
+  float2 a[RB][RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int c = 0; c < RB; ++c) {
+      const int i = bi * RB + r, j = bj * RB + c;
+      a[r][c] = (i < UP && j < UP) ? A[i * UP + j] : make_float2(0.f, 0.f);
+    }
+  int st = ST_OK;
+  for (int p = 0; p < U; ++p) {
+    float2 *rowp = rc + (p & 1) * 2 * UP, *colp = rowp + UP;
+    const int pb = p / RB, pr = p - pb * RB;
+    if (bi == pb) {  // row p
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r == pr)
+#pragma unroll
+          for (int c = 0; c < RB; ++c)
+            if (bj * RB + c < UP) rowp[bj * RB + c] = a[r][c];
+    }
+    if (bj == pb) {  // column p
+#pragma unroll
+      for (int c = 0; c < RB; ++c)
+        if (c == pr)
+#pragma unroll
+          for (int r = 0; r < RB; ++r)
+            if (bi * RB + r < UP) colp[bi * RB + r] = a[r][c];
+    }
+    __syncthreads();
+    const float piv = rowp[p].x;
+    if (!(piv > 0.f) || !isfinite(piv)) {  // uniform over the CTA
+      st = ST_NOT_PD;
+      break;
+    }
+    const float ip = 1.f / piv;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      const int i = bi * RB + r;
+      if (i >= U) continue;
+      const float2 f = cscale(colp[i], ip);
+#pragma unroll
+      for (int c = 0; c < RB; ++c) {
+        const int j = bj * RB + c;
+        if (j >= U) continue;
+        if (i == p) {
+          a[r][c] = (j == p) ? make_float2(ip, 0.f) : cscale(rowp[j], ip);
+        } else if (j == p) {
+          a[r][c] = cscale(colp[i], -ip);
+        } else {
+          cmsub(a[r][c], f, rowp[j]);
+        }
+      }
+    }
+  }
+  __syncthreads();  // the last pivot's readers are done with rc; A is rewritten
+#pragma unroll
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int c = 0; c < RB; ++c) {
+      const int i = bi * RB + r, j = bj * RB + c;
+      if (i < UP && j < UP) A[i * UP + j] = a[r][c];
+    }
+  __syncthreads();
+  return st;
+}
+
 // t = tr(Q^H Q) of Thm. 1 for T = A^{-1}: Lemma 1, tr(T) - kappa ||T||_F^2,
 // unless its subtraction cancels (kappa ||T||_F^2 > kLemmaMaxRatio tr(T));
 // then the definition through Eq. (14), tr(T G T) = sum_ij (T G)_ij conj(T_ij).

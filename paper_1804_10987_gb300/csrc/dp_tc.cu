@@ -48,8 +48,8 @@ struct TcGeo {
   static constexpr int PS = P_PAD ? M2 + 1 : M2;
   static_assert(P_PAD || (M2 % 32 == 0), "swizzled P needs 32-float rows");
   static_assert(LARGE || (size_t)NG * M2 * PS * 4 <= REGION, "P fits the region");
-  static_assert(!LARGE || ((size_t)UP * PS * 4 <= REGION && (size_t)UP * UP * 8 <= REGION),
-                "half of P and the inverse fit the region");
+  static_assert(!LARGE || ((size_t)UP * PS * 4 <= REGION && (size_t)UP * (UP + 4) * 8 <= REGION),
+                "half of P, the inverse and its row / column buffers fit the region");
   // realified users per apply K-block (one 128-byte row of 16-bit entries)
   static constexpr int KBLK = (2 * UP + 63) / 64;
   // refinement keeps dz [NG][K][UP] (K <= 64) in the region
@@ -385,7 +385,8 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
         if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
         else sc = sqrtf(d.rho2_sys / (d.Es * t));
       } else {
-        if (st == ST_OK) st = cta_gj_inverse<UP>(Aw, U, tid);
+        if (st == ST_OK)  // row / column exchange buffers after A in the region
+          st = cta_gj_inverse_reg<UP>(Aw, U, tid, Aw + UP * UP);
         if (st == ST_OK) {
           const float t = cta_trace_tgt<UP>(Aw, Gs, d.kappa, U, sc_s + NG, tid);
           if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
