@@ -254,23 +254,43 @@ __device__ int cta_gj_inverse_reg(float2 *A, int U, int tid, float2 *rc) {
       break;
     }
     const float ip = 1.f / piv;
+    // every owned element takes the elimination update with row p and its
+    // row's multiplier (zero past U: pads stay exact); then the owners of
+    // row p and column p overwrite those entries with the pivot formulas
+    float2 rowv[RB], fv[RB];
+#pragma unroll
+    for (int c = 0; c < RB; ++c) {
+      const int j = bj * RB + c;
+      rowv[c] = j < U ? rowp[j] : make_float2(0.f, 0.f);
+    }
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
       const int i = bi * RB + r;
-      if (i >= U) continue;
-      const float2 f = cscale(colp[i], ip);
+      fv[r] = i < U ? cscale(colp[i], ip) : make_float2(0.f, 0.f);
+    }
 #pragma unroll
-      for (int c = 0; c < RB; ++c) {
-        const int j = bj * RB + c;
-        if (j >= U) continue;
-        if (i == p) {
-          a[r][c] = (j == p) ? make_float2(ip, 0.f) : cscale(rowp[j], ip);
-        } else if (j == p) {
-          a[r][c] = cscale(colp[i], -ip);
-        } else {
-          cmsub(a[r][c], f, rowp[j]);
-        }
-      }
+    for (int r = 0; r < RB; ++r)
+#pragma unroll
+      for (int c = 0; c < RB; ++c) cmsub(a[r][c], fv[r], rowv[c]);
+    if (bi == pb) {  // row p: T_pj = A_pj / A_pp, T_pp = 1 / A_pp
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        if (r == pr)
+#pragma unroll
+          for (int c = 0; c < RB; ++c) {
+            const int j = bj * RB + c;
+            if (j < U) a[r][c] = (j == p) ? make_float2(ip, 0.f) : cscale(rowv[c], ip);
+          }
+    }
+    if (bj == pb) {  // column p: T_ip = -A_ip / A_pp
+#pragma unroll
+      for (int c = 0; c < RB; ++c)
+        if (c == pr)
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            const int i = bi * RB + r;
+            if (i < U && i != p) a[r][c] = cscale(colp[i], -ip);
+          }
     }
   }
   __syncthreads();  // the last pivot's readers are done with rc; A is rewritten
