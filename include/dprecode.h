@@ -226,7 +226,8 @@ const char *dp_batch_describe(dp_batch_t b);
  * cells overlap on the GPU, the slots of one cell stay in order) and retires
  * them when they complete, recording the latency from submission to the
  * observed completion.  Every request runs the same kernels as dp_precode
- * with the cell's precision, so its result does not depend on the mix.
+ * with the cell's precision (or, with cache_solve, the cached-solve kernels),
+ * so its result does not depend on the mix.
  * The paper has no serving layer; this packages its per-slot precoder
  * (Sec. IV) for an arrival process of slots. */
 typedef struct {
@@ -235,6 +236,13 @@ typedef struct {
   int max_inflight;    /* requests on the GPU at once, 1..1024 */
   size_t arena_bytes;  /* device memory for request outputs and status */
   int auto_release;    /* 1: a request's output is freed as soon as it completes */
+  int cache_solve;     /* 1: per cell, everything that depends on the channel
+                          alone -- G, T = (G + kappa I)^{-1} and the scale
+                          (Thm. 1, Lemma 1) -- is computed in FP32 on the first
+                          request after each dp_server_set_channel and kept;
+                          every request then only whitens (z = T s) and applies
+                          (FP32).  FD-WF clusters with B_c < U stay per request.
+                          0: every request runs the dp_precode kernels */
 } dp_server_config;
 
 typedef struct {

@@ -64,4 +64,13 @@ cudaError_t launch_batch_fd_small(int bcp, const InstDesc *insts, const WorkItem
                                   int n_items, int *queue, int Kmax, int grid, cudaStream_t s);
 int fd_small_max_blocks_per_sm(int bcp, int Kmax);
 
+// Served path's solve cache: T = (G + kappa I)^{-1}, scale and status per
+// system from an FP32 Gram (layout of launch_gram), and the per-request
+// whitening z = T s with the request's status and scale (0 when failed).
+cudaError_t launch_cache_invert(const SysDesc &d, int UP, const float2 *G, float2 *T, float *scale,
+                                int *status, cudaStream_t s);
+cudaError_t launch_cache_whiten(const SysDesc &d, int UP, const float2 *T, const float *cscale,
+                                const int *cstatus, const float2 *S, float2 *Z, float *rscale,
+                                int *status, cudaStream_t s);
+
 }  // namespace dp

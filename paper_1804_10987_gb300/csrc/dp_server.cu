@@ -100,9 +100,16 @@ struct Cell {
   const void *H = nullptr;
   int stream = 0;
   size_t x_bytes = 0, st_bytes = 0;
-  // streaming-form workspace (cells whose antenna block exceeds shared memory)
+  // streaming-form workspace (cells whose antenna block exceeds shared memory,
+  // and cells with a solve cache)
   float2 *w_G = nullptr, *w_Z = nullptr;
   float *w_scale = nullptr;
+  // solve cache: T, scale and status per system for the channel c_H
+  bool cached = false;
+  const void *c_H = nullptr;
+  float2 *c_T = nullptr;
+  float *c_scale = nullptr;
+  int *c_st = nullptr;
 };
 
 struct Request {
@@ -183,6 +190,23 @@ cudaError_t launch_request(dp_server *sv, Request *r) {
   float2 *X = reinterpret_cast<float2 *>(sv->arena.ptr(r->x_off));
   int *status = reinterpret_cast<int *>(sv->arena.ptr(r->st_off));
   cudaError_t e = cudaSuccess;
+  if (c.cached) {
+    // the channel's Gram, inverse and scale once per channel; then z = T s
+    // and the apply for every request
+    if (r->H != c.c_H) {
+      e = dp::launch_gram(d, c.UP, H, c.w_G, st);
+      if (e == cudaSuccess) e = dp::launch_cache_invert(d, c.UP, c.w_G, c.c_T, c.c_scale, c.c_st, st);
+      if (e == cudaSuccess) c.c_H = r->H;
+    }
+    if (e == cudaSuccess && c.has_small)
+      e = dp::launch_fd_small(dp::InstDesc{d, H, S, X, status, nullptr}, c.bcp, st);
+    if (e == cudaSuccess)
+      e = dp::launch_cache_whiten(d, c.UP, c.c_T, c.c_scale, c.c_st, S, c.w_Z, c.w_scale, status,
+                                  st);
+    if (e == cudaSuccess && c.d.K > 0) e = dp::launch_apply(d, c.UP, H, c.w_Z, c.w_scale, X, st);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev, st);
+    return e;
+  }
   if (c.has_small) e = dp::launch_fd_small(dp::InstDesc{d, H, S, X, status, nullptr}, c.bcp, st);
   if (e != cudaSuccess || c.all_small) {
   } else if (c.tc)
@@ -394,15 +418,25 @@ dp_status dp_server_add_cell(dp_server_t sv, const dp_plan_desc *desc, const voi
     return DP_ERR_OOM;
   }
   cudaMemcpy(c.d_off, c.off.data(), sizeof(int) * c.off.size(), cudaMemcpyHostToDevice);
-  if (!c.tc && !c.fused) {
+  c.cached = sv->cfg.cache_solve != 0 && !c.all_small;
+  if (c.cached || (!c.tc && !c.fused)) {
     const size_t ns = (size_t)d.n_sc * c.nsys;
-    if (cudaMalloc(&c.w_G, sizeof(float2) * ns * d.U * d.U) != cudaSuccess ||
-        cudaMalloc(&c.w_Z, sizeof(float2) * ns * d.K * d.U) != cudaSuccess ||
-        cudaMalloc(&c.w_scale, sizeof(float) * ns) != cudaSuccess) {
+    bool ok = cudaMalloc(&c.w_G, sizeof(float2) * ns * d.U * d.U) == cudaSuccess &&
+              cudaMalloc(&c.w_Z, sizeof(float2) * ns * d.K * d.U) == cudaSuccess &&
+              cudaMalloc(&c.w_scale, sizeof(float) * ns) == cudaSuccess;
+    if (ok && c.cached)
+      ok = cudaMalloc(&c.c_T, sizeof(float2) * ns * d.U * d.U) == cudaSuccess &&
+           cudaMalloc(&c.c_scale, sizeof(float) * ns) == cudaSuccess &&
+           cudaMalloc(&c.c_st, sizeof(int) * ns) == cudaSuccess;
+    if (!ok) {
       cudaGetLastError();
       cudaFree(c.d_off);
       cudaFree(c.w_G);
       cudaFree(c.w_Z);
+      cudaFree(c.w_scale);
+      cudaFree(c.c_T);
+      cudaFree(c.c_scale);
+      cudaFree(c.c_st);
       return DP_ERR_OOM;
     }
   }
@@ -417,6 +451,7 @@ dp_status dp_server_set_channel(dp_server_t sv, int cell, const void *H) {
   std::lock_guard<std::mutex> lk(sv->mu);
   if (cell < 0 || cell >= (int)sv->cells.size()) return DP_ERR_INVALID_ARG;
   sv->cells[cell].H = H;
+  sv->cells[cell].c_H = nullptr;  // the cached solve belongs to the old channel
   return DP_OK;
 }
 
@@ -565,6 +600,9 @@ dp_status dp_server_destroy(dp_server_t sv) {
     cudaFree(c.w_G);
     cudaFree(c.w_Z);
     cudaFree(c.w_scale);
+    cudaFree(c.c_T);
+    cudaFree(c.c_scale);
+    cudaFree(c.c_st);
   }
   for (auto s : sv->streams) cudaStreamDestroy(s);
   cudaGetLastError();

@@ -45,7 +45,8 @@ class PlanDesc(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("streams", ctypes.c_int), ("max_inflight", ctypes.c_int),
-                ("arena_bytes", ctypes.c_size_t), ("auto_release", ctypes.c_int)]
+                ("arena_bytes", ctypes.c_size_t), ("auto_release", ctypes.c_int),
+                ("cache_solve", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -388,10 +389,10 @@ class Server:
     server's arena."""
 
     def __init__(self, streams: int = 8, max_inflight: int = 32, arena_bytes: int = 1 << 30,
-                 auto_release: bool = False, device: int = 0):
+                 auto_release: bool = False, device: int = 0, cache_solve: bool = False):
         self._lib = load()
         cfg = ServerConfig(int(device), int(streams), int(max_inflight), int(arena_bytes),
-                           int(bool(auto_release)))
+                           int(bool(auto_release)), int(bool(cache_solve)))
         h = ctypes.c_void_p()
         _check(self._lib.dp_server_create(ctypes.byref(cfg), ctypes.byref(h)), "dp_server_create")
         self._h = h

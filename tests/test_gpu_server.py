@@ -132,3 +132,71 @@ def test_server_rejects_bad_cells():
     with pytest.raises(dp.DPError):
         srv.add_cell(dict(U=8, B=64, C=3, n_sc=4, K=14), H)
     srv.close()
+
+
+def test_cached_solve_across_channel_switches():
+    """cache_solve: the Gram, inverse and scale are computed once per channel
+    (FP32) and reused; requests before and after each switch match the oracle
+    on the channel they were submitted on."""
+    import torch
+    cells = make_cells(6, 61)
+    p_mrt = synth.make_problem(16, 128, 4, 24, 14, 64, 10.0, seed=6161, mode="wf")
+    cells.append((p_mrt, dict(U=16, B=128, C=4, n_sc=24, K=14, mode="mrt", prec="fp16",
+                              N0=p_mrt.N0, tau=0.125), torch.from_numpy(p_mrt.H).cuda()))
+    cs = [3, 40, 5, 80]  # FD-WF with B_c < U clusters (those stay per request)
+    p_fd = synth.make_problem(16, sum(cs), len(cs), 20, 14, 64, 10.0, seed=6162, mode="fdwf",
+                              cluster_sizes=cs)
+    cells.append((p_fd, dict(U=16, B=sum(cs), C=len(cs), n_sc=20, K=14, mode="fdwf", prec="bf16",
+                             N0=p_fd.N0, tau=0.125, cluster_sizes=cs),
+                  torch.from_numpy(p_fd.H).cuda()))
+    srv = dp.Server(streams=3, max_inflight=8, arena_bytes=256 << 20, cache_solve=True)
+    ids = [srv.add_cell(desc, H) for _, desc, H in cells]
+    H2 = [synth.rayleigh(p.n_sc, p.B, p.U, synth.rng(700 + i)) for i, (p, _, _) in enumerate(cells)]
+    H2d = [torch.from_numpy(h).cuda() for h in H2]
+    plan = []  # (cell, channel index) in submission order
+    for c in range(len(cells)):
+        plan += [(c, 0)] * 3 + [(c, 1)] * 2 + [(c, 0)]
+    order = np.random.default_rng(7).permutation(len(cells))  # interleave the cells
+    seq = [x for k in range(6) for c in order for x in [plan[c * 6 + k]]]
+    S, rids = [], []
+    for c, ch in seq:
+        p, _, H = cells[c]
+        srv.set_channel(ids[c], H if ch == 0 else H2d[c])
+        s = symbols(p, 5000 + len(S))
+        S.append(s)
+        rids.append(srv.submit(ids[c], s))
+    srv.drain()
+    for (c, ch), s, rid in zip(seq, S, rids):
+        p, desc, _ = cells[c]
+        x = torch.empty((p.n_sc, p.K, p.B), dtype=torch.complex64, device="cuda")
+        srv.copy_result(rid, x)
+        assert srv.result(rid) == 0
+        srv.release(rid)
+        ref = oracle.precode(p.H if ch == 0 else H2[c], s.cpu().numpy(), p.cluster_sizes,
+                             desc["mode"], N0=p.N0, tau=0.125, nthreads=8)
+        err = rel_err_per_sc(x.cpu().numpy(), ref["X"]).max()
+        assert err <= TOL_FP32, (c, ch, desc["mode"], desc["prec"], err)
+    srv.close()
+
+
+def test_cached_solve_flags_a_bad_request_only():
+    import torch
+    cells = make_cells(1, 62, prec_cycle=("fp16",))
+    p, desc, H = cells[0]
+    srv = dp.Server(streams=1, max_inflight=4, arena_bytes=64 << 20, cache_solve=True)
+    cid = srv.add_cell(desc, H)
+    good = symbols(p, 1)
+    bad = good.clone()
+    bad[3, 2, 1] = float("nan")
+    rids = [srv.submit(cid, s) for s in (good, bad, good)]
+    srv.drain()
+    outs = []
+    for rid in rids:
+        x = torch.empty((p.n_sc, p.K, p.B), dtype=torch.complex64, device="cuda")
+        srv.copy_result(rid, x)
+        outs.append((srv.result(rid), x))
+    assert outs[0][0] == 0 and outs[2][0] == 0 and outs[1][0] == dp.NONFINITE
+    assert torch.equal(outs[0][1], outs[2][1])
+    assert torch.all(outs[1][1][3] == 0)
+    assert torch.equal(outs[1][1][:3], outs[0][1][:3])
+    srv.close()
