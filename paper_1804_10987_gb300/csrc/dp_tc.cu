@@ -143,6 +143,173 @@ __device__ __forceinline__ bool tc_wait_mma(TcCtx &cx, int buf) {
   return ok;
 }
 
+// ---- apply on the tensor cores ----------------------------------------------
+// For the group's systems [0, nact) described in shared memory (first antenna,
+// antennas, subcarrier, skip flag, status, scale, z [NG][K][UP]): systems with
+// a failed status get zeroed rows, the others x = scale H^H z.
+// Per 128-antenna M-tile: D[b][n] = sum_j A[b][j] Bm[n][j] with A[b][2u + r]
+// = (Re, Im) H[b][u] and, for symbol q of a chunk of 16, Bm[2q] = (Re z_u,
+// Im z_u)_u and Bm[2q + 1] = (Im z_u, -Re z_u)_u, so that D[b][2q] + i
+// D[b][2q + 1] = sum_u conj(H[b][u]) z_q[u].  The realified users j run in
+// K-blocks of 64 (one 128-byte swizzled row), accumulated in TMEM.  Split
+// FP16 keeps ~22 bits: A = A_hi + 2^-11 A_lo, z = z_hi + z_lo, D = A_hi z_hi
+// + A_hi z_lo + A_lo (2^-11 z_hi); z is first normalized by a power of two.
+template <int UP>
+__device__ bool tc_apply(TcCtx &cx, const SysDesc &d, const float2 *__restrict__ H,
+                         float2 *__restrict__ X, int nact, bool ok) {
+  using T = TcGeo<UP>;
+  constexpr int NG = T::NG;
+  const TcSmem &L = cx.L;
+  unsigned char *base = cx.base;
+  const float2 *Zs = reinterpret_cast<const float2 *>(base + L.Z);
+  float *sc_s = reinterpret_cast<float *>(base + L.scale);
+  const int *st_s = reinterpret_cast<const int *>(base + L.status);
+  const int *lo_s = reinterpret_cast<const int *>(base + L.info);
+  const int *nr_s = lo_s + NG, *n_s = nr_s + NG, *sk_s = n_s + NG;
+  uint64_t *bar_mma = reinterpret_cast<uint64_t *>(base + L.bars) + 1;
+  const uint32_t taddr = cx.taddr;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int U = d.U, K = d.K;
+  unsigned char *a_hi = base + L.region;
+  unsigned char *a_lo = a_hi + TILE_BYTES;
+  unsigned char *b_op = a_hi + 2 * TILE_BYTES;  // hi, lo, hi * 2^-11
+  const uint32_t a_hi_u = smem_u32(a_hi), a_lo_u = smem_u32(a_lo), b_u = smem_u32(b_op);
+  const uint32_t idesc_ap = tc::idesc_f16(128, 32, false);
+  for (int s = 0; s < nact && ok; ++s) {
+    if (sk_s[s] || nr_s[s] == 0) continue;
+    float2 *Xn = X + (size_t)n_s[s] * K * d.B + lo_s[s];
+    if (st_s[s] != ST_OK) {
+      zero_rows<UP>(nr_s[s], K, X + (size_t)n_s[s] * K * d.B, d.B, lo_s[s], tid);
+      continue;
+    }
+    const float2 *zs = Zs + s * K * UP;
+    // power-of-two normalization of z for the FP16 range
+    float zmax = 0.f;
+    for (int e = tid; e < K * UP; e += NT)
+      if (e % UP < U) zmax = fmaxf(zmax, fmaxf(fabsf(zs[e].x), fabsf(zs[e].y)));
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, o));
+    __syncthreads();
+    if (lane == 0) sc_s[NG + warp] = zmax;  // scratch slots after the scales
+    __syncthreads();
+    float zm = 0.f;
+    for (int w = 0; w < NT / 32; ++w) zm = fmaxf(zm, sc_s[NG + w]);
+    int zexp = 0;
+    if (zm > 0.f) frexpf(zm, &zexp);        // zm = f 2^zexp, f in [0.5, 1)
+    const float zn = ldexpf(1.f, -zexp);    // z * zn in (-1, 1)
+    const float out_scale = ldexpf(sc_s[s], zexp);
+    const float2 *hsys = H + ((size_t)n_s[s] * d.B + lo_s[s]) * U;
+    for (int q0 = 0; q0 < K && ok; q0 += 16) {
+      const int nq = min(16, K - q0);
+      for (int m0 = 0; m0 < nr_s[s] && ok; m0 += 128) {
+        const int mrows = min(128, nr_s[s] - m0);
+        for (int kb = 0; kb < T::KBLK && ok; ++kb) {
+          const int ent = min(64, 2 * UP - 64 * kb);  // realified entries in this block
+          const int ksteps = (ent + 15) / 16;
+          __syncthreads();  // the previous MMAs and readout are done with A, B, TMEM
+          // B operands: 32 rows x 8 chunks of 8 entries (4 users x Re/Im)
+          for (int e = tid; e < 32 * 8; e += NT) {
+            const int row = e >> 3, c8 = e & 7;
+            const int q = row >> 1, im = row & 1;
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int u = 32 * kb + 4 * c8 + j;
+              float2 z = make_float2(0.f, 0.f);
+              if (q < nq && u < U && 8 * c8 < ent) z = zs[(q0 + q) * UP + u];
+              z.x *= zn;
+              z.y *= zn;
+              v[2 * j] = im ? z.y : z.x;
+              v[2 * j + 1] = im ? -z.x : z.y;
+            }
+            uint4 hi, lo, hs;
+            uint32_t *ph = &hi.x, *pl = &lo.x, *ps = &hs.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+              const float2 hf = __half22float2(h2);
+              const __half2 l2 = __floats2half2_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
+              const __half2 s2 = __floats2half2_rn(hf.x * 0x1p-11f, hf.y * 0x1p-11f);
+              ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
+              pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
+              ps[j] = *reinterpret_cast<const uint32_t *>(&s2);
+            }
+            const uint32_t off = tc::sw128_offset(row, c8);
+            *reinterpret_cast<uint4 *>(b_op + off) = hi;
+            *reinterpret_cast<uint4 *>(b_op + BOP + off) = lo;
+            *reinterpret_cast<uint4 *>(b_op + 2 * BOP + off) = hs;
+          }
+          // A tiles: rows = antennas, 16-byte chunk c8 = users 4c8..4c8+3 of
+          // the block; zero beyond the block's entries and the tile's rows
+          for (int e = tid; e < 128 * 8; e += NT) {
+            const int r = e >> 3, c8 = e & 7;
+            uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
+            if (8 * c8 < ent) {
+              float v[8];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int u = 32 * kb + 4 * c8 + j;
+                const float2 h = (r < mrows && u < U)
+                                     ? __ldg(hsys + (size_t)(m0 + r) * U + u)
+                                     : make_float2(0.f, 0.f);
+                v[2 * j] = h.x;
+                v[2 * j + 1] = h.y;
+              }
+              uint32_t *ph = &hi.x, *pl = &lo.x;
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+                const float2 hf = __half22float2(h2);
+                const __half2 l2 = __floats2half2_rn((v[2 * j] - hf.x) * 0x1p11f,
+                                                     (v[2 * j + 1] - hf.y) * 0x1p11f);
+                ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
+              }
+            }
+            const uint32_t off = tc::sw128_offset(r, c8);
+            *reinterpret_cast<uint4 *>(a_hi + off) = hi;
+            *reinterpret_cast<uint4 *>(a_lo + off) = lo;
+          }
+          fence_proxy_async_smem();
+          __syncthreads();
+          if (tid == 0) {
+            tc::fence_after_sync();
+            for (int kk = 0; kk < ksteps; ++kk) {
+              const uint32_t ko = kk * 32;
+              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko),
+                          tc::desc_kmajor_sw128(b_u + ko), idesc_ap, kb > 0 || kk > 0);
+              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko),
+                          tc::desc_kmajor_sw128(b_u + BOP + ko), idesc_ap, true);
+              tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_lo_u + ko),
+                          tc::desc_kmajor_sw128(b_u + 2 * BOP + ko), idesc_ap, true);
+            }
+            tc::commit(bar_mma);
+          }
+          ++cx.mma_commits[0];
+          ok = tc_wait_mma(cx, 0);
+          tc::fence_after_sync();
+        }
+        if (!ok) break;
+        if (warp < 4) {
+          float v[32];
+          tc::tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16), v);
+          const int r = 32 * warp + lane;
+          if (r < mrows) {
+            float2 *xc = Xn + m0 + r;
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+              if (q < nq) xc[(size_t)(q0 + q) * d.B] = make_float2(v[2 * q] * out_scale,
+                                                                   v[2 * q + 1] * out_scale);
+          }
+        }
+        tc::fence_before_sync();
+      }
+    }
+  }
+  __syncthreads();
+  return ok;
+}
+
 // Systems [sys0, sys0 + nact) of one instance (nact <= NG): Gram on the tensor
 // cores, solve, apply.  Returns false if a bounded wait gave up (the
 // systems' outputs are then zeroed and their status set to ST_TIMEOUT).
@@ -416,154 +583,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   fence_proxy_async_smem();
   __syncthreads();
 
-  // ---- apply on the tensor cores --------------------------------------------
-  // Per 128-antenna M-tile: D[b][n] = sum_j A[b][j] Bm[n][j] with A[b][2u + r]
-  // = (Re, Im) H[b][u] and, for symbol q of a chunk of 16, Bm[2q] = (Re z_u,
-  // Im z_u)_u and Bm[2q + 1] = (Im z_u, -Re z_u)_u, so that D[b][2q] + i
-  // D[b][2q + 1] = sum_u conj(H[b][u]) z_q[u].  The realified users j run in
-  // K-blocks of 64 (one 128-byte swizzled row), accumulated in TMEM.  Split
-  // FP16 keeps ~22 bits: A = A_hi + 2^-11 A_lo, z = z_hi + z_lo, D = A_hi z_hi
-  // + A_hi z_lo + A_lo (2^-11 z_hi); z is first normalized by a power of two.
-  auto apply_all = [&]() {
-    unsigned char *a_hi = base + L.region;
-    unsigned char *a_lo = a_hi + TILE_BYTES;
-    unsigned char *b_op = a_hi + 2 * TILE_BYTES;  // hi, lo, hi * 2^-11
-    const uint32_t a_hi_u = smem_u32(a_hi), a_lo_u = smem_u32(a_lo), b_u = smem_u32(b_op);
-    const uint32_t idesc_ap = tc::idesc_f16(128, 32, false);
-    for (int s = 0; s < nact && ok; ++s) {
-      if (sk_s[s] || nr_s[s] == 0) continue;
-      float2 *Xn = X + (size_t)n_s[s] * K * d.B + lo_s[s];
-      if (st_s[s] != ST_OK) {
-        zero_rows<UP>(nr_s[s], K, X + (size_t)n_s[s] * K * d.B, d.B, lo_s[s], tid);
-        continue;
-      }
-      const float2 *zs = Zs + s * K * UP;
-      // power-of-two normalization of z for the FP16 range
-      float zmax = 0.f;
-      for (int e = tid; e < K * UP; e += NT)
-        if (e % UP < U) zmax = fmaxf(zmax, fmaxf(fabsf(zs[e].x), fabsf(zs[e].y)));
-#pragma unroll
-      for (int o = 16; o >= 1; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, o));
-      __syncthreads();
-      if (lane == 0) sc_s[NG + warp] = zmax;  // scratch slots after the scales
-      __syncthreads();
-      float zm = 0.f;
-      for (int w = 0; w < NT / 32; ++w) zm = fmaxf(zm, sc_s[NG + w]);
-      int zexp = 0;
-      if (zm > 0.f) frexpf(zm, &zexp);        // zm = f 2^zexp, f in [0.5, 1)
-      const float zn = ldexpf(1.f, -zexp);    // z * zn in (-1, 1)
-      const float out_scale = ldexpf(sc_s[s], zexp);
-      const float2 *hsys = H + ((size_t)n_s[s] * d.B + lo_s[s]) * U;
-      for (int q0 = 0; q0 < K && ok; q0 += 16) {
-        const int nq = min(16, K - q0);
-        for (int m0 = 0; m0 < nr_s[s] && ok; m0 += 128) {
-          const int mrows = min(128, nr_s[s] - m0);
-          for (int kb = 0; kb < T::KBLK && ok; ++kb) {
-            const int ent = min(64, 2 * UP - 64 * kb);  // realified entries in this block
-            const int ksteps = (ent + 15) / 16;
-            __syncthreads();  // the previous MMAs and readout are done with A, B, TMEM
-            // B operands: 32 rows x 8 chunks of 8 entries (4 users x Re/Im)
-            for (int e = tid; e < 32 * 8; e += NT) {
-              const int row = e >> 3, c8 = e & 7;
-              const int q = row >> 1, im = row & 1;
-              float v[8];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const int u = 32 * kb + 4 * c8 + j;
-                float2 z = make_float2(0.f, 0.f);
-                if (q < nq && u < U && 8 * c8 < ent) z = zs[(q0 + q) * UP + u];
-                z.x *= zn;
-                z.y *= zn;
-                v[2 * j] = im ? z.y : z.x;
-                v[2 * j + 1] = im ? -z.x : z.y;
-              }
-              uint4 hi, lo, hs;
-              uint32_t *ph = &hi.x, *pl = &lo.x, *ps = &hs.x;
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
-                const float2 hf = __half22float2(h2);
-                const __half2 l2 = __floats2half2_rn(v[2 * j] - hf.x, v[2 * j + 1] - hf.y);
-                const __half2 s2 = __floats2half2_rn(hf.x * 0x1p-11f, hf.y * 0x1p-11f);
-                ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
-                pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
-                ps[j] = *reinterpret_cast<const uint32_t *>(&s2);
-              }
-              const uint32_t off = tc::sw128_offset(row, c8);
-              *reinterpret_cast<uint4 *>(b_op + off) = hi;
-              *reinterpret_cast<uint4 *>(b_op + BOP + off) = lo;
-              *reinterpret_cast<uint4 *>(b_op + 2 * BOP + off) = hs;
-            }
-            // A tiles: rows = antennas, 16-byte chunk c8 = users 4c8..4c8+3 of
-            // the block; zero beyond the block's entries and the tile's rows
-            for (int e = tid; e < 128 * 8; e += NT) {
-              const int r = e >> 3, c8 = e & 7;
-              uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
-              if (8 * c8 < ent) {
-                float v[8];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  const int u = 32 * kb + 4 * c8 + j;
-                  const float2 h = (r < mrows && u < U)
-                                       ? __ldg(hsys + (size_t)(m0 + r) * U + u)
-                                       : make_float2(0.f, 0.f);
-                  v[2 * j] = h.x;
-                  v[2 * j + 1] = h.y;
-                }
-                uint32_t *ph = &hi.x, *pl = &lo.x;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                  const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
-                  const float2 hf = __half22float2(h2);
-                  const __half2 l2 = __floats2half2_rn((v[2 * j] - hf.x) * 0x1p11f,
-                                                       (v[2 * j + 1] - hf.y) * 0x1p11f);
-                  ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
-                  pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
-                }
-              }
-              const uint32_t off = tc::sw128_offset(r, c8);
-              *reinterpret_cast<uint4 *>(a_hi + off) = hi;
-              *reinterpret_cast<uint4 *>(a_lo + off) = lo;
-            }
-            fence_proxy_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-              tc::fence_after_sync();
-              for (int kk = 0; kk < ksteps; ++kk) {
-                const uint32_t ko = kk * 32;
-                tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko),
-                            tc::desc_kmajor_sw128(b_u + ko), idesc_ap, kb > 0 || kk > 0);
-                tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_hi_u + ko),
-                            tc::desc_kmajor_sw128(b_u + BOP + ko), idesc_ap, true);
-                tc::mma_f16(taddr, tc::desc_kmajor_sw128(a_lo_u + ko),
-                            tc::desc_kmajor_sw128(b_u + 2 * BOP + ko), idesc_ap, true);
-              }
-              tc::commit(bar_mma);
-            }
-            ++cx.mma_commits[0];
-            ok = tc_wait_mma(cx, 0);
-            tc::fence_after_sync();
-          }
-          if (!ok) break;
-          if (warp < 4) {
-            float v[32];
-            tc::tmem_ld32(taddr + ((uint32_t)(32 * warp) << 16), v);
-            const int r = 32 * warp + lane;
-            if (r < mrows) {
-              float2 *xc = Xn + m0 + r;
-#pragma unroll
-              for (int q = 0; q < 16; ++q)
-                if (q < nq) xc[(size_t)(q0 + q) * d.B] = make_float2(v[2 * q] * out_scale,
-                                                                     v[2 * q + 1] * out_scale);
-            }
-          }
-          tc::fence_before_sync();
-        }
-      }
-    }
-    __syncthreads();
-  };
-  apply_all();
+  ok = tc_apply<UP>(cx, d, H, X, nact, ok);
 
   if constexpr (!T::LARGE) {
     if (d.refine && !d.mrt && ok) {
@@ -616,7 +636,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
       }
       fence_proxy_async_smem();
       __syncthreads();
-      apply_all();
+      ok = tc_apply<UP>(cx, d, H, X, nact, ok);
     }
   }
 
