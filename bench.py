@@ -64,6 +64,9 @@ def parse():
                     help="skip the serving sweep (Poisson arrivals)")
     ap.add_argument("--serve-requests", type=int, default=1500,
                     help="requests per arrival rate in the serving sweep")
+    ap.add_argument("--serving-burst", type=int, default=0, metavar="N",
+                    help="only this: N requests submitted at once to the solve-cached FP32 "
+                         "server over the serving cells (i.i.d. channels); one JSON line")
     return ap.parse_args()
 
 
@@ -422,6 +425,38 @@ def measure_serving(dp, synth, torch, n_req):
     return out
 
 
+def serving_burst(n):
+    """N requests submitted at t = 0 to the solve-cached FP32 server over the
+    32 serving cells (shapes of the batched configuration, K = 14, i.i.d.
+    channels, one channel per cell): throughput and latency of a burst."""
+    import numpy as np
+    import torch
+
+    from paper_1804_10987_gb300 import dp, synth
+    shapes = synth.c4_instance_shapes(32, synth.seed_for(5))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.seed_for(5, 1))
+    N0 = synth.n0_from_snr(10.0)
+    cells = []
+    for sh in shapes:
+        H = synth.torch_channel(sh["n_sc"], sh["B"], sh["U"], "iid", gen, "cuda")
+        S = synth.torch_symbols(64, (sh["n_sc"], 14, sh["U"]), gen, "cuda")
+        cells.append((sh, H, S))
+    srv = dp.Server(streams=16, max_inflight=64, arena_bytes=16 << 30, auto_release=True,
+                    cache_solve=True)
+    ids = [srv.add_cell(dict(U=sh["U"], B=sh["B"], C=sh["C"], n_sc=sh["n_sc"], K=14,
+                             mode=sh["mode"], prec="fp32", N0=N0, tau=0.125), H)
+           for sh, H, _ in cells]
+    cell_of = np.random.default_rng(1).integers(0, len(cells), n)
+    srv.replay([ids[c] for c in cell_of], [cells[c][2] for c in cell_of], np.zeros(n))
+    st = srv.stats()
+    srv.close()
+    print(json.dumps({"serving_burst": n, "cache_solve": True, "prec": "fp32",
+                      "subcarriers_per_s": st["subcarriers"] / max(st["wall_s"], 1e-9),
+                      "wall_ms": st["wall_s"] * 1e3, "p50_ms": st["p50_ms"],
+                      "p99_ms": st["p99_ms"], "failed": st["failed"]}))
+
+
 def our_arm(args):
     import numpy as np
     import torch
@@ -608,6 +643,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.serving_burst > 0:
+        serving_burst(args.serving_burst)
     else:
         our_arm(args)
 

@@ -221,20 +221,22 @@ const char *dp_batch_describe(dp_batch_t b);
  * into an output X [n_sc][K][B] that the server places in its device arena.
  * A worker thread admits pending requests in arrival order whenever fewer
  * than max_inflight are on the GPU and the arena has room for the request's
- * output and status (admission by free device memory), launches them on the
- * cell's stream (cells are spread over the streams: requests of different
- * cells overlap on the GPU, the slots of one cell stay in order) and retires
- * them when they complete, recording the latency from submission to the
- * observed completion.  Every request runs the same kernels as dp_precode
+ * output and status (admission by free device memory), launches them
+ * round-robin over the server's streams (requests overlap on the GPU, those
+ * of one cell included; cells in the streaming FP32 form, whose workspace is
+ * per cell, keep their slots in order on one stream) and retires them when
+ * they complete, recording the latency from submission to the observed
+ * completion.  Every request runs the same kernels as dp_precode
  * with the cell's precision (or, with cache_solve, the cached-solve kernels),
  * so its result does not depend on the mix.
  * The paper has no serving layer; this packages its per-slot precoder
  * (Sec. IV) for an arrival process of slots. */
 typedef struct {
   int device;          /* CUDA device the server runs on */
-  int streams;         /* CUDA streams the cells are spread over, 1..64 */
+  int streams;         /* CUDA streams the requests are spread over, 1..64 */
   int max_inflight;    /* requests on the GPU at once, 1..1024 */
-  size_t arena_bytes;  /* device memory for request outputs and status */
+  size_t arena_bytes;  /* device memory for request outputs, status and, with
+                          cache_solve, each request's z and scale */
   int auto_release;    /* 1: a request's output is freed as soon as it completes */
   int cache_solve;     /* 1: per cell, everything that depends on the channel
                           alone -- G, T = (G + kappa I)^{-1} and the scale

@@ -6,11 +6,18 @@
 // a buffer the server takes from its device arena.  A dispatcher thread
 // admits pending requests in arrival order whenever an in-flight slot and
 // enough arena memory are free (admission by free device memory), launches
-// them on the cell's CUDA stream (cells are spread over the streams, so
-// requests of different cells overlap on the GPU while the slots of one cell
-// stay in order), and retires completed ones: status copied out, latency
-// recorded (arrival -> completion observed on the host), output buffer kept
-// until the caller releases it (or released at once in auto-release mode).
+// them round-robin over the server's CUDA streams (so requests overlap on the
+// GPU, those of one cell included; only cells in the streaming FP32 form,
+// whose workspace is per cell, keep their slots in order on the cell's
+// stream), and retires completed ones: status copied out, latency recorded
+// (arrival -> completion observed on the host), output buffer kept until the
+// caller releases it (or released at once in auto-release mode).
+//
+// Solve cache: a cell's T = (G + kappa I)^{-1} and scale are recomputed on
+// the cell's own cache stream when a request arrives with a channel other
+// than the cached one; the recomputation first waits for every in-flight
+// request of the cell (they still read the old T), and every request waits for
+// the newest recomputation before it whitens.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -99,17 +106,22 @@ struct Cell {
   int bcp = 0;
   const void *H = nullptr;
   int stream = 0;
+  bool overlap = false;  // requests of this cell may run concurrently
   size_t x_bytes = 0, st_bytes = 0;
+  size_t w_bytes = 0;  // per-request workspace: z [sys][K][U], then scale [sys]
   // streaming-form workspace (cells whose antenna block exceeds shared memory,
   // and cells with a solve cache)
   float2 *w_G = nullptr, *w_Z = nullptr;
   float *w_scale = nullptr;
-  // solve cache: T, scale and status per system for the channel c_H
+  // solve cache: T, scale and status per system for the channel c_H, written
+  // on c_stream; c_ready marks the newest recomputation
   bool cached = false;
   const void *c_H = nullptr;
   float2 *c_T = nullptr;
   float *c_scale = nullptr;
   int *c_st = nullptr;
+  cudaStream_t c_stream = nullptr;
+  cudaEvent_t c_ready = nullptr;
 };
 
 struct Request {
@@ -118,7 +130,7 @@ struct Request {
   const void *S;
   const void *H;  // channel at submission
   Clock::time_point t_arrival, t_done;
-  size_t x_off = SIZE_MAX, st_off = SIZE_MAX;
+  size_t x_off = SIZE_MAX, st_off = SIZE_MAX, w_off = SIZE_MAX;
   cudaEvent_t ev = nullptr;
   int status = 0;
   bool done = false, released = false;
@@ -141,6 +153,7 @@ struct dp_server {
   std::unordered_map<uint64_t, Request *> all;  // not yet released
   std::vector<double> lat_ms;
   uint64_t next_id = 1;
+  uint64_t next_stream = 0;  // round-robin stream choice
   long long subcarriers_done = 0;
   int inflight_peak = 0;
   int failures = 0;
@@ -183,7 +196,8 @@ dp::SysDesc sys_of(const Cell &c, const void *H) {
 
 cudaError_t launch_request(dp_server *sv, Request *r) {
   Cell &c = sv->cells[r->cell];
-  cudaStream_t st = sv->streams[c.stream];
+  cudaStream_t st = c.overlap ? sv->streams[sv->next_stream++ % sv->streams.size()]
+                              : sv->streams[c.stream];
   const dp::SysDesc d = sys_of(c, r->H);
   const float2 *H = static_cast<const float2 *>(r->H);
   const float2 *S = static_cast<const float2 *>(r->S);
@@ -193,17 +207,25 @@ cudaError_t launch_request(dp_server *sv, Request *r) {
   if (c.cached) {
     // the channel's Gram, inverse and scale once per channel; then z = T s
     // and the apply for every request
+    const size_t ns = (size_t)c.d.n_sc * c.nsys;
+    float2 *Z = reinterpret_cast<float2 *>(sv->arena.ptr(r->w_off));
+    float *zscale = reinterpret_cast<float *>(Z + ns * c.d.K * c.d.U);
     if (r->H != c.c_H) {
-      e = dp::launch_gram(d, c.UP, H, c.w_G, st);
-      if (e == cudaSuccess) e = dp::launch_cache_invert(d, c.UP, c.w_G, c.c_T, c.c_scale, c.c_st, st);
+      // the cell's in-flight requests still read the old T
+      for (const Request *q : sv->inflight)
+        if (q->cell == r->cell && e == cudaSuccess) e = cudaStreamWaitEvent(c.c_stream, q->ev, 0);
+      if (e == cudaSuccess) e = dp::launch_gram(d, c.UP, H, c.w_G, c.c_stream);
+      if (e == cudaSuccess)
+        e = dp::launch_cache_invert(d, c.UP, c.w_G, c.c_T, c.c_scale, c.c_st, c.c_stream);
+      if (e == cudaSuccess) e = cudaEventRecord(c.c_ready, c.c_stream);
       if (e == cudaSuccess) c.c_H = r->H;
     }
     if (e == cudaSuccess && c.has_small)
       e = dp::launch_fd_small(dp::InstDesc{d, H, S, X, status, nullptr}, c.bcp, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c.c_ready, 0);
     if (e == cudaSuccess)
-      e = dp::launch_cache_whiten(d, c.UP, c.c_T, c.c_scale, c.c_st, S, c.w_Z, c.w_scale, status,
-                                  st);
-    if (e == cudaSuccess && c.d.K > 0) e = dp::launch_apply(d, c.UP, H, c.w_Z, c.w_scale, X, st);
+      e = dp::launch_cache_whiten(d, c.UP, c.c_T, c.c_scale, c.c_st, S, Z, zscale, status, st);
+    if (e == cudaSuccess) e = dp::launch_apply(d, c.UP, H, Z, zscale, X, st);
     if (e == cudaSuccess) e = cudaEventRecord(r->ev, st);
     return e;
   }
@@ -245,6 +267,8 @@ void retire(dp_server *sv) {
     }
     if (r->status) ++sv->failures;
     sv->arena.release(r->st_off, c.st_bytes);
+    if (r->w_off != SIZE_MAX) sv->arena.release(r->w_off, c.w_bytes);
+    r->w_off = SIZE_MAX;
     r->done = true;
     sv->lat_ms.push_back(
         std::chrono::duration<double, std::milli>(r->t_done - r->t_arrival).count());
@@ -274,14 +298,23 @@ void admit(dp_server *sv) {
       sv->arena.release(xo, c.x_bytes);
       break;
     }
+    const size_t wo = c.w_bytes ? sv->arena.alloc(c.w_bytes) : SIZE_MAX;
+    if (c.w_bytes && wo == SIZE_MAX) {
+      sv->arena.release(xo, c.x_bytes);
+      sv->arena.release(so, c.st_bytes);
+      break;
+    }
     r->x_off = xo;
     r->st_off = so;
+    r->w_off = wo;
     if (cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess ||
         launch_request(sv, r) != cudaSuccess) {
       cudaGetLastError();
       sv->error = true;
       sv->arena.release(xo, c.x_bytes);
       sv->arena.release(so, c.st_bytes);
+      if (wo != SIZE_MAX) sv->arena.release(wo, c.w_bytes);
+      r->w_off = SIZE_MAX;
       if (r->ev) cudaEventDestroy(r->ev);
       r->ev = nullptr;
       r->done = true;
@@ -419,15 +452,28 @@ dp_status dp_server_add_cell(dp_server_t sv, const dp_plan_desc *desc, const voi
   }
   cudaMemcpy(c.d_off, c.off.data(), sizeof(int) * c.off.size(), cudaMemcpyHostToDevice);
   c.cached = sv->cfg.cache_solve != 0 && !c.all_small;
-  if (c.cached || (!c.tc && !c.fused)) {
-    const size_t ns = (size_t)d.n_sc * c.nsys;
-    bool ok = cudaMalloc(&c.w_G, sizeof(float2) * ns * d.U * d.U) == cudaSuccess &&
-              cudaMalloc(&c.w_Z, sizeof(float2) * ns * d.K * d.U) == cudaSuccess &&
-              cudaMalloc(&c.w_scale, sizeof(float) * ns) == cudaSuccess;
+  // the streaming FP32 form keeps G and z per cell, so its requests stay in
+  // order on the cell's stream; every other form may overlap
+  c.overlap = c.cached || c.tc || c.fused;
+  const size_t ns = (size_t)d.n_sc * c.nsys;
+  if (c.cached) {
+    c.w_bytes = sizeof(float2) * ns * d.K * d.U + sizeof(float) * ns;
+    if (c.x_bytes + c.st_bytes + c.w_bytes + 768 > sv->arena.bytes()) {
+      cudaFree(c.d_off);
+      return DP_ERR_OOM;
+    }
+  }
+  if (c.cached || !c.overlap) {
+    bool ok = cudaMalloc(&c.w_G, sizeof(float2) * ns * d.U * d.U) == cudaSuccess;
+    if (ok && !c.cached)
+      ok = cudaMalloc(&c.w_Z, sizeof(float2) * ns * d.K * d.U) == cudaSuccess &&
+           cudaMalloc(&c.w_scale, sizeof(float) * ns) == cudaSuccess;
     if (ok && c.cached)
       ok = cudaMalloc(&c.c_T, sizeof(float2) * ns * d.U * d.U) == cudaSuccess &&
            cudaMalloc(&c.c_scale, sizeof(float) * ns) == cudaSuccess &&
-           cudaMalloc(&c.c_st, sizeof(int) * ns) == cudaSuccess;
+           cudaMalloc(&c.c_st, sizeof(int) * ns) == cudaSuccess &&
+           cudaStreamCreateWithFlags(&c.c_stream, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c.c_ready, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       cudaFree(c.d_off);
@@ -437,6 +483,7 @@ dp_status dp_server_add_cell(dp_server_t sv, const dp_plan_desc *desc, const voi
       cudaFree(c.c_T);
       cudaFree(c.c_scale);
       cudaFree(c.c_st);
+      if (c.c_stream) cudaStreamDestroy(c.c_stream);
       return DP_ERR_OOM;
     }
   }
@@ -603,6 +650,8 @@ dp_status dp_server_destroy(dp_server_t sv) {
     cudaFree(c.c_T);
     cudaFree(c.c_scale);
     cudaFree(c.c_st);
+    if (c.c_ready) cudaEventDestroy(c.c_ready);
+    if (c.c_stream) cudaStreamDestroy(c.c_stream);
   }
   for (auto s : sv->streams) cudaStreamDestroy(s);
   cudaGetLastError();
