@@ -3,14 +3,20 @@
 //   Q_c = (H_c^H H_c + kappa_c I_{B_c})^{-1} H_c^H,
 //   x_c = sqrt(rho_c^2 / (tr(Q_c^H Q_c) Es)) Q_c s,
 // which replaces the U x U inverse by a B_c x B_c one.  One warp per
-// cluster system (B_c <= 32), lane a = antenna a of the cluster:
+// cluster system (B_c <= BCP <= 32).  Lane (a, part) = (lane % BCP,
+// lane / BCP) works on antenna a of the cluster and on the users
+// u = part (mod 32 / BCP) of every chunk, so that all 32 lanes share the
+// user loops when BCP < 32:
 //   1. G'[a][b] = sum_u conj(H[a][u]) H[b][u] over user chunks of 16 staged in
-//      shared memory (row a of G' in lane a's registers),
-//   2. in-place Gauss-Jordan inverse of A' = G' + kappa_c I in registers,
+//      shared memory; the parts' partial rows are summed by shuffles, after
+//      which every part holds row a of G' in registers,
+//   2. in-place Gauss-Jordan inverse of A' = G' + kappa_c I in registers
+//      (row a of every part, identical across the parts),
 //   3. Q[a][u] = sum_b T'[a][b] conj(H[b][u]) chunk by chunk; tr(Q^H Q) is
 //      accumulated as the definition (no Lemma 1 subtraction to cancel) and
-//      x[k][a] += sum_u Q[a][u] s_k[u] into per-warp shared accumulators,
-//   4. scale = sqrt(rho_c^2 / (Es tr(Q^H Q))), X[k][lo + a] = scale x[k][a].
+//      x[k][a] += sum_u Q[a][u] s_k[u] into per-part shared accumulators,
+//   4. scale = sqrt(rho_c^2 / (Es tr(Q^H Q))), X[k][lo + a] = scale times the
+//      sum of the parts' accumulators, in part order.
 #include "dp_blocks.cuh"
 #include "dp_internal.h"
 
@@ -21,26 +27,31 @@ constexpr int UC = 16;          // users per staged chunk
 constexpr int FD_WARPS = 4;     // warps (systems in flight) per CTA
 
 __host__ __device__ constexpr size_t fd_warp_floats(int BCP, int K) {
-  // H chunk [BCP][UC] + S chunk [K][UC] + x accumulators [K][BCP] (complex)
-  return 2 * ((size_t)BCP * UC + (size_t)K * UC + (size_t)K * BCP);
+  // H chunk [BCP][UC] + S chunk [K][UC] + x accumulators [32 / BCP][K][BCP]
+  // (complex)
+  return 2 * ((size_t)BCP * UC + (size_t)K * UC + (size_t)K * 32);
 }
 
 template <int BCP>
 __device__ void fd_small_system(const InstDesc &in, int sys, float2 *ws, int lane) {
+  constexpr int PARTS = 32 / BCP;  // lanes sharing one antenna row
+  constexpr int UPL = UC / PARTS;  // users of a chunk per lane
+  static_assert(32 % BCP == 0 && UC % PARTS == 0, "lane split");
   const SysDesc &d = in.d;
   const int n = sys / d.nsys, g = sys - n * d.nsys;
   int lo, hi;
   sys_rows(d, g, lo, hi);
   const int nb = hi - lo, U = d.U, K = d.K;
   if (!(nb < U && nb <= BCP)) return;  // not a small-cluster system
+  const int a = lane % BCP, part = lane / BCP;
   float2 *Hc = ws;                      // [BCP][UC]
   float2 *Sc = Hc + BCP * UC;           // [K][UC]
-  float2 *Xa = Sc + K * UC;             // [K][BCP]
+  float2 *Xa = Sc + K * UC;             // [PARTS][K][BCP]
   const float2 *Hn = in.H + ((size_t)n * d.B + lo) * U;
   const float2 *Sn = in.S + (size_t)n * K * U;
   bool fin = true;
 
-  // 1. antenna-side Gram, row `lane`
+  // 1. antenna-side Gram, row a (this part's users)
   float2 row[BCP];
 #pragma unroll
   for (int b = 0; b < BCP; ++b) row[b] = make_float2(0.f, 0.f);
@@ -57,36 +68,46 @@ __device__ void fd_small_system(const InstDesc &in, int sys, float2 *ws, int lan
       Hc[e] = v;
     }
     __syncwarp();
-    float2 my[UC];
+    float2 my[UPL];
 #pragma unroll
-    for (int u = 0; u < UC; ++u) my[u] = lane < BCP ? Hc[lane * UC + u] : make_float2(0.f, 0.f);
+    for (int uu = 0; uu < UPL; ++uu) my[uu] = Hc[a * UC + part + uu * PARTS];
 #pragma unroll
     for (int b = 0; b < BCP; ++b) {
       if (b < nb) {
 #pragma unroll
-        for (int u = 0; u < UC; ++u) cmac_cj(row[b], my[u], Hc[b * UC + u]);
+        for (int uu = 0; uu < UPL; ++uu) cmac_cj(row[b], my[uu], Hc[b * UC + part + uu * PARTS]);
       }
+    }
+  }
+  // the parts' partial rows: a butterfly over the lanes a, a + BCP, ...
+#pragma unroll
+  for (int o = BCP; o < 32; o <<= 1) {
+#pragma unroll
+    for (int b = 0; b < BCP; ++b) {
+      row[b].x += __shfl_xor_sync(FULL, row[b].x, o);
+      row[b].y += __shfl_xor_sync(FULL, row[b].y, o);
     }
   }
   for (int e = lane; e < K * U; e += 32) fin = fin && cfinite(__ldg(Sn + e));
   fin = __all_sync(FULL, fin);
-  if (lane >= nb) {
+  if (a >= nb) {
 #pragma unroll
     for (int b = 0; b < BCP; ++b) row[b] = make_float2(0.f, 0.f);
   }
 #pragma unroll
   for (int b = 0; b < BCP; ++b)
-    if (b == lane) {
+    if (b == a) {
       row[b].y = 0.f;
       row[b].x += d.kappa;  // A' = G' + kappa_c I
     }
 
-  // 2. T' = A'^{-1}
+  // 2. T' = A'^{-1} (pivot rows come from the lanes of part 0)
   int st = fin ? ST_OK : ST_NONFINITE;
-  if (st == ST_OK && !warp_gj_inverse<BCP>(row, lane, nb)) st = ST_NOT_PD;
+  if (st == ST_OK && !warp_gj_inverse<BCP>(row, a, nb)) st = ST_NOT_PD;
 
   // 3. Q = T' H_c^H by user chunks; t = ||Q||_F^2; x accumulators
-  for (int e = lane; e < K * BCP; e += 32) Xa[e] = make_float2(0.f, 0.f);
+  float2 *Xp = Xa + part * K * BCP;  // this part's accumulators
+  for (int e = lane; e < PARTS * K * BCP; e += 32) Xa[e] = make_float2(0.f, 0.f);
   float tq = 0.f;
   if (st == ST_OK) {
     for (int u0 = 0; u0 < U; u0 += UC) {
@@ -101,40 +122,49 @@ __device__ void fd_small_system(const InstDesc &in, int sys, float2 *ws, int lan
         Sc[e] = u < uc ? __ldg(Sn + (size_t)k * U + u0 + u) : make_float2(0.f, 0.f);
       }
       __syncwarp();
-      float2 q[UC];
+      float2 q[UPL];
 #pragma unroll
-      for (int u = 0; u < UC; ++u) q[u] = make_float2(0.f, 0.f);
+      for (int uu = 0; uu < UPL; ++uu) q[uu] = make_float2(0.f, 0.f);
 #pragma unroll
       for (int b = 0; b < BCP; ++b) {
         if (b < nb) {
 #pragma unroll
-          for (int u = 0; u < UC; ++u) cmac(q[u], row[b], cconj(Hc[b * UC + u]));
+          for (int uu = 0; uu < UPL; ++uu)
+            cmac(q[uu], row[b], cconj(Hc[b * UC + part + uu * PARTS]));
         }
       }
-      if (lane < nb) {
+      if (a < nb) {
 #pragma unroll
-        for (int u = 0; u < UC; ++u) tq = fmaf(q[u].x, q[u].x, fmaf(q[u].y, q[u].y, tq));
+        for (int uu = 0; uu < UPL; ++uu) tq = fmaf(q[uu].x, q[uu].x, fmaf(q[uu].y, q[uu].y, tq));
         for (int k = 0; k < K; ++k) {
-          float2 acc = Xa[k * BCP + lane];
+          float2 acc = Xp[k * BCP + a];
 #pragma unroll
-          for (int u = 0; u < UC; ++u) cmac(acc, q[u], Sc[k * UC + u]);
-          Xa[k * BCP + lane] = acc;
+          for (int uu = 0; uu < UPL; ++uu) cmac(acc, q[uu], Sc[k * UC + part + uu * PARTS]);
+          Xp[k * BCP + a] = acc;
         }
       }
     }
   }
-  const float t = warp_sum(lane < nb ? tq : 0.f);
+  const float t = warp_sum(a < nb ? tq : 0.f);
   float sc = 0.f;
   if (st == ST_OK) {
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
     else sc = sqrtf(d.rho2_sys / (d.Es * t));
   }
   __syncwarp();
-  // 4. x_c = scale Q_c s
-  if (lane < nb) {
-    float2 *Xn = in.X + (size_t)n * K * d.B + lo + lane;
-    for (int k = 0; k < K; ++k)
-      Xn[(size_t)k * d.B] = st == ST_OK ? cscale(Xa[k * BCP + lane], sc) : make_float2(0.f, 0.f);
+  // 4. x_c = scale Q_c s, the parts summed in order
+  if (part == 0 && a < nb) {
+    float2 *Xn = in.X + (size_t)n * K * d.B + lo + a;
+    for (int k = 0; k < K; ++k) {
+      float2 v = Xa[k * BCP + a];
+#pragma unroll
+      for (int pp = 1; pp < PARTS; ++pp) {
+        const float2 w = Xa[(pp * K + k) * BCP + a];
+        v.x += w.x;
+        v.y += w.y;
+      }
+      Xn[(size_t)k * d.B] = st == ST_OK ? cscale(v, sc) : make_float2(0.f, 0.f);
+    }
   }
   if (lane == 0) {
     in.status[sys] = st;
