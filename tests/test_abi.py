@@ -85,3 +85,32 @@ def test_null_arguments():
     assert lib.dp_plan_create(None, None, None) == dp.INVALID_ARG
     assert lib.dp_precode(None, None, None, None) == dp.INVALID_ARG
     assert lib.dp_status_get(None, None) == dp.INVALID_ARG
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's field offsets and
+    sizes (a C program built against include/dprecode.h prints them)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    structs = {"dp_plan_desc": dp.PlanDesc, "dp_server_config": dp.ServerConfig,
+               "dp_server_stats_t": dp.ServerStats}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "dprecode.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        src.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            src.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    src.append("  return 0;\n}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.splitlines())
+    for cname, cls in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
