@@ -70,6 +70,28 @@ def parse():
     return ap.parse_args()
 
 
+def job_time_ms(ms, world, device):
+    """The job's time for N ranks: the slowest rank's (max over ranks)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed per second of the
+    job's time (each rank processes its own units: weak scaling)."""
+    return units_per_rank * world / (ms / 1e3)
+
+
+def rank_seed(synth, rank):
+    """Seed of a rank's input shard: every rank precodes its own slots."""
+    return synth.seed_for(2, 500 + rank)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -476,7 +498,7 @@ def our_arm(args):
     stream = torch.cuda.current_stream()
 
     gen = torch.Generator(device="cuda")
-    gen.manual_seed(synth.seed_for(2, 500 + rank))
+    gen.manual_seed(rank_seed(synth, rank))
     H = synth.torch_channel(n_sc, B, U, "iid", gen, "cuda")
     S = synth.torch_symbols(w["qam"], (n_sc, K, U), gen, "cuda")
     X = torch.empty((n_sc, K, B), dtype=torch.complex64, device="cuda")
@@ -516,12 +538,8 @@ def our_arm(args):
         torch.cuda.synchronize()
         barrier()
         clocks = sampler.stop() if sampler else None
-        ms_total = t0.elapsed_time(t1)
+        ms_total = job_time_ms(t0.elapsed_time(t1), world, "cuda")
         launch_ms = [a.elapsed_time(b) for a, b in ev]
-        if world > 1:
-            t = torch.tensor([ms_total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_total = float(t.item())
         return plan, ms_total, launch_ms, clocks
 
     # algorithmic bytes of one launch: H once + S + X
@@ -542,12 +560,12 @@ def our_arm(args):
         X_plain = torch.empty_like(X)
         pplan, p_ms, p_launch, _ = time_path("fp32", X_plain, False)
         pplan.close()
-        plain = {"value": n_sc * args.steps * world / (p_ms / 1e3), "unit": "subcarriers/s",
+        plain = {"value": job_rate(n_sc * args.steps, world, p_ms), "unit": "subcarriers/s",
                  "ms_per_step": p_ms / args.steps, "dtype": "f32",
                  "roofline": roofline_of("fp32", p_launch)}
     plan, ms_total, launch_ms, clocks = time_path(args.prec, X, True)
     ms_step = ms_total / args.steps
-    value = n_sc * args.steps * world / (ms_total / 1e3)
+    value = job_rate(n_sc * args.steps, world, ms_total)
     roofline = roofline_of(args.prec, launch_ms)
     library = None
     if not args.no_library:
@@ -573,12 +591,8 @@ def our_arm(args):
             plan.precode_host(Hh, Sh, Xh, WORKLOAD["n_sc"])
         b.record(stream)
         torch.cuda.synchronize()
-        e_ms = a.elapsed_time(b)
-        if world > 1:
-            t = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": n_sc * e_steps * world / (e_ms / 1e3), "unit": "subcarriers/s",
+        e_ms = job_time_ms(a.elapsed_time(b), world, "cuda")
+        e2e = {"value": job_rate(n_sc * e_steps, world, e_ms), "unit": "subcarriers/s",
                "h2d_bytes_per_step": H.numel() * 8 + S.numel() * 8,
                "d2h_bytes_per_step": X.numel() * 8, "steps": e_steps}
         assert np.isfinite(Xh[:2].numpy()).all()
