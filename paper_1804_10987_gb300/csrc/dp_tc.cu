@@ -1,6 +1,7 @@
 // dp_tc.cu -- the reduced-precision fused precoder: Gram contraction on the
 // 5th-generation tensor cores (tcgen05, BF16 or FP16 inputs, FP32
-// accumulation in TMEM), solve and apply in FP32.
+// accumulation in TMEM), solve in FP32, apply as a split-FP16 tensor-core
+// product.
 //
 // One CTA takes a group of NG = 128 / (2 UP) systems.  The complex Gram of a
 // system is one real product: with P = R R^T for R = [Re H; Im H] (2U rows,
@@ -13,10 +14,11 @@
 // so that the conversion of chunk c+1 overlaps the MMAs of chunk c), four
 // MMAs of K = 16 per chunk accumulating in TMEM.
 // Then: TMEM -> shared P -> G, warp-per-system Gauss-Jordan solve in
-// registers (Thm. 1, Lemma 1 through tr(T G T), z = A^{-1} s), and the FP32
-// apply x_c = scale H_c^H z over antenna rows bulk-copied again (from L2)
-// into padded shared rows.  The 32 KB tile region is reused for P and for
-// the apply rows, which keeps three to four CTAs on an SM.
+// registers (Thm. 1, Lemma 1 through tr(T G T), z = A^{-1} s; a CTA solve for
+// U > 32), and the apply x_c = scale H_c^H z (tc_apply): 128-antenna tiles of
+// H split into FP16 hi / lo parts, z split likewise, three MMAs per K-step
+// into TMEM, scaled on the way out.  The 32 KB tile region is reused for P
+// and for the apply operands, which keeps three to four CTAs on an SM.
 #include "dp_blocks.cuh"
 #include "dp_internal.h"
 #include "dp_tc.cuh"
