@@ -115,8 +115,17 @@ def config_dict(args, world, slots):
                         f"K={w['K']} {w['qam']}-QAM SNR {w['snr_db']:g} dB iid Rayleigh",
             "mode": args.mode, "prec": args.prec, "slots_per_step": slots,
             "subcarriers_per_step": w["n_sc"] * slots,
-            "l2": "inputs larger than L2 (331 MB per step of 8 slots vs 129 MB L2)",
+            "l2": l2_note(slots),
             "parallelism": f"replicas x{world}"}
+
+
+def l2_note(slots):
+    """Whether one step's inputs (H and S of every slot) exceed the 129 MB L2,
+    so that timed steps read HBM without an L2 flush."""
+    w = WORKLOAD
+    mb = slots * w["n_sc"] * (8 * w["U"] * w["B"] + 8 * w["K"] * w["U"]) / 1e6
+    rel = "larger than" if mb > 129 else "not larger than"
+    return f"inputs {rel} L2 ({mb:.0f} MB per step of {slots} slots vs 129 MB L2)"
 
 
 # ----------------------------------------------------------------- clocks ----
@@ -234,6 +243,7 @@ def reference_arm(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(config_dict(args, 1, 1), slots_per_step=1, prec="f64 oracle",
+                           l2="host run of the CPU oracle (no GPU caches involved)",
                            subcarriers_per_step=WORKLOAD["n_sc"]),
             "cpu_baseline": {"value": rate, "unit": "subcarriers/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
