@@ -237,14 +237,16 @@ typedef struct {
   int max_inflight;    /* requests on the GPU at once, 1..1024 */
   size_t arena_bytes;  /* device memory for request outputs, status and, with
                           cache_solve, each request's z and scale */
-  int auto_release;    /* 1: a request's output is freed as soon as it completes */
+  int auto_release;    /* 1: a request's output is freed as soon as it completes;
+                          0: kept until dp_server_release (other values: invalid) */
   int cache_solve;     /* 1: per cell, everything that depends on the channel
                           alone -- G, T = (G + kappa I)^{-1} and the scale
                           (Thm. 1, Lemma 1) -- is computed in FP32 on the first
                           request after each dp_server_set_channel and kept;
                           every request then only whitens (z = T s) and applies
                           (FP32).  FD-WF clusters with B_c < U stay per request.
-                          0: every request runs the dp_precode kernels */
+                          0: every request runs the dp_precode kernels (other
+                          values: invalid) */
 } dp_server_config;
 
 typedef struct {

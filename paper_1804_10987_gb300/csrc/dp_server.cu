@@ -366,7 +366,9 @@ dp_status dp_server_create(const dp_server_config *cfg, dp_server_t *out) {
   if (!out) return DP_ERR_INVALID_ARG;
   *out = nullptr;
   if (!cfg || cfg->max_inflight < 1 || cfg->max_inflight > 1024 || cfg->streams < 1 ||
-      cfg->streams > 64 || cfg->arena_bytes < 4096)
+      cfg->streams > 64 || cfg->arena_bytes < 4096 ||
+      (cfg->auto_release != 0 && cfg->auto_release != 1) ||
+      (cfg->cache_solve != 0 && cfg->cache_solve != 1))
     return DP_ERR_INVALID_ARG;
   if (cudaSetDevice(cfg->device) != cudaSuccess) {
     cudaGetLastError();

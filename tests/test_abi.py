@@ -114,3 +114,37 @@ def test_ctypes_structs_match_the_header(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(max_inflight=0), dict(max_inflight=1025), dict(streams=0), dict(streams=65),
+    dict(arena_bytes=4095), dict(auto_release=2), dict(auto_release=-1), dict(cache_solve=2),
+    dict(cache_solve=-1),
+])
+def test_server_config_validation_on_host(kw):
+    lib = dp.load()
+    base = dict(device=0, streams=4, max_inflight=8, arena_bytes=1 << 20, auto_release=0,
+                cache_solve=0)
+    base.update(kw)
+    cfg = dp.ServerConfig(*[base[f] for f, _ in dp.ServerConfig._fields_])
+    h = ctypes.c_void_p()
+    assert lib.dp_server_create(ctypes.byref(cfg), ctypes.byref(h)) == dp.INVALID_ARG
+    assert not h.value
+
+
+def test_server_null_handles():
+    lib = dp.load()
+    rid = ctypes.c_ulonglong()
+    st = dp.ServerStats()
+    assert lib.dp_server_create(None, None) == dp.INVALID_ARG
+    assert lib.dp_server_destroy(None) == dp.INVALID_ARG
+    assert lib.dp_server_add_cell(None, None, None, None) == dp.INVALID_ARG
+    assert lib.dp_server_set_channel(None, 0, None) == dp.INVALID_ARG
+    assert lib.dp_server_submit(None, 0, None, ctypes.byref(rid)) == dp.INVALID_ARG
+    assert lib.dp_server_drain(None) == dp.INVALID_ARG
+    assert lib.dp_server_result(None, ctypes.c_ulonglong(1), None, None) == dp.INVALID_ARG
+    assert lib.dp_server_copy_result(None, ctypes.c_ulonglong(1), None, 0) == dp.INVALID_ARG
+    assert lib.dp_server_release(None, ctypes.c_ulonglong(1)) == dp.INVALID_ARG
+    assert lib.dp_server_replay(None, 0, None, None, None, None) == dp.INVALID_ARG
+    assert lib.dp_server_stats(None, ctypes.byref(st)) == dp.INVALID_ARG
+    assert lib.dp_server_reset_stats(None) == dp.INVALID_ARG
