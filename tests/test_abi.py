@@ -148,3 +148,42 @@ def test_server_null_handles():
     assert lib.dp_server_replay(None, 0, None, None, None, None) == dp.INVALID_ARG
     assert lib.dp_server_stats(None, ctypes.byref(st)) == dp.INVALID_ARG
     assert lib.dp_server_reset_stats(None) == dp.INVALID_ARG
+
+
+def _desc(**kw):
+    base = dict(U=8, B=64, C=2, n_sc=4, K=2, mode=1, prec=0, rho2=1.0, N0=0.1, Es=1.0,
+                tau=0.125, refine=0)
+    base.update(kw)
+    return dp.PlanDesc(base["U"], base["B"], base["C"], None, base["n_sc"], base["K"],
+                       base["mode"], base["prec"], base["rho2"], base["N0"], base["Es"],
+                       base["tau"], base["refine"])
+
+
+def test_batch_validation_on_host():
+    lib = dp.load()
+    h = ctypes.c_void_p()
+    arr = (dp.PlanDesc * 2)(_desc(), _desc())
+    assert lib.dp_batch_create(None, 1, None, ctypes.byref(h)) == dp.INVALID_ARG
+    assert lib.dp_batch_create(arr, 0, None, ctypes.byref(h)) == dp.INVALID_ARG
+    assert lib.dp_batch_create(arr, 2, None, None) == dp.INVALID_ARG
+    for bad, code in ((dict(U=0), dp.INVALID_ARG), (dict(C=3), dp.PARTITION),
+                      (dict(mode=0, U=8, B=6, C=1), dp.UNSUPPORTED)):
+        arr = (dp.PlanDesc * 2)(_desc(), _desc(**bad))  # the second instance is invalid
+        assert lib.dp_batch_create(arr, 2, None, ctypes.byref(h)) == code, bad
+        assert not h.value
+    assert lib.dp_batch_destroy(None) == dp.INVALID_ARG
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(U=0), dp.INVALID_ARG), (dict(K=65), dp.INVALID_ARG), (dict(mode=9), dp.INVALID_ARG),
+    (dict(prec=2), dp.UNSUPPORTED), (dict(refine=1), dp.UNSUPPORTED), (dict(C=3), dp.PARTITION),
+    (dict(mode=0, U=8, B=6, C=1), dp.UNSUPPORTED),
+    # workspace beyond the static array: 4000 subcarriers of U = 64 need 131 MB of G
+    (dict(U=64, B=128, C=1, n_sc=4000), dp.UNSUPPORTED),
+    (dict(n_sc=0), dp.OK),  # nothing to do, nothing enqueued
+    (dict(), dp.INVALID_ARG),  # a valid description with null device arrays
+])
+def test_noalloc_validation_on_host(kw, code):
+    lib = dp.load()
+    d = _desc(**kw)
+    assert lib.dp_precode_noalloc(ctypes.byref(d), None, None, None, None, None) == code
