@@ -1,5 +1,7 @@
 """Continuous-batching server: results identical alone and in a concurrent
-mix, admission bounded by the arena, channel switches, latency accounting."""
+mix, admission bounded by the arena, channel switches, latency accounting,
+and the per-channel solve cache (outputs against the oracle across channel
+switches, overlapping requests of one cell, a bad request flagged alone)."""
 import numpy as np
 import pytest
 
