@@ -330,7 +330,7 @@ def _c(a):
     return a[..., 0] + 1j * a[..., 1]
 
 
-@pytest.mark.parametrize("case", ["wf", "zf", "fdwf_tau1_c2"])
+@pytest.mark.parametrize("case", ["wf", "zf", "fdwf_tau1_c2", "mrt"])
 def test_hand_worked_examples(case):
     d = _gold()
     H = _c(d["H_BU"])[None]
@@ -340,6 +340,8 @@ def test_hand_worked_examples(case):
         out = oracle.precode(H, S, [2], "wf", N0=d["N0"], rho2=d["rho2"], Es=d["Es"])
     elif case == "zf":
         out = oracle.precode(H, S, [2], "zf", N0=0.0, rho2=d["rho2"], Es=d["Es"])
+    elif case == "mrt":
+        out = oracle.precode(H, S, [2], "mrt", N0=d["N0"], rho2=d["rho2"], Es=d["Es"])
     else:
         out = oracle.precode(H, S, e["cluster_sizes"], "fdwf", N0=d["N0"], rho2=d["rho2"],
                              Es=d["Es"], tau=e["tau"])
