@@ -100,14 +100,25 @@ typedef struct {
   float N0;                  /* noise variance per entry >= 0 (WF, FD) */
   float Es;                  /* symbol energy E|s_u|^2 > 0 (1 for normalized QAM) */
   float tau;                 /* FD-WF tau_c >= 0 (Eq. (16)); ignored otherwise */
-  int refine;                /* 1 with BF16/FP16: one step of iterative refinement
-                                of z against the reduced-precision Gram -- the
-                                residual r = s - (H H^H + kappa I) z from the exact
-                                FP32 H with FP32 accumulation, z += (G_lp +
-                                kappa I)^{-1} r, then the apply again (U <= 32,
-                                else DP_ERR_UNSUPPORTED); the precoding factor
-                                keeps the low-precision inverse's value;
-                                ignored for DP_FP32; 0: none */
+  int refine;                /* BF16/FP16 only (ignored for DP_FP32 and MRT): one
+                                step of iterative refinement of z against the
+                                reduced-precision Gram -- the residual
+                                r = s - (H H^H + kappa I) z from the exact FP32 H
+                                with FP32 accumulation, z += (G_lp + kappa I)^{-1} r,
+                                then the apply again; the precoding factor keeps
+                                the low-precision inverse's value.
+                                0 (default): automatic -- a system with
+                                eps ||G||_F ||A^{-1}||_F / U >= 2e-3, eps the 16-bit
+                                type's unit roundoff (2^-8 BF16, 2^-11 FP16), i.e.
+                                whose 16-bit Gram could move the output by about
+                                5e-4 or more (ZF with few antennas per user,
+                                strongly correlated channels), is escalated: its
+                                Gram is recomputed in FP32 and solved again, which
+                                also corrects the precoding factor (refining z
+                                alone leaves the factor's error, which comes from
+                                the low-precision inverse);
+                                1: the refinement step for every subcarrier;
+                                -1: neither */
 } dp_plan_desc;
 
 typedef struct dp_plan *dp_plan_t;
@@ -169,6 +180,18 @@ dp_status dp_precode(dp_plan_t plan, const void *H, const void *S, void *X);
  * cannot be allocated. */
 dp_status dp_precode_host(dp_plan_t plan, const void *H, const void *S, void *X, int chunk_sc);
 
+/* Failure injection for tests of the timeout path (Sec. IV-B's pipeline has
+ * no counterpart; this checks the library's own bounded waits).  While
+ * microseconds > 0, every later dp_precode of this plan that runs the
+ * warp-specialized tensor-core kernel (BF16/FP16, users padded to 8 or 16,
+ * 1 <= K <= 16, U even) makes that kernel's MMA-issuing thread first wait,
+ * for that long, on a flag that nothing sets.  The wait then runs out as any
+ * bounded on-device wait does: the kernel's other roles stop, its copies and
+ * MMAs in flight land, its TMEM is freed, and every subcarrier of the call
+ * ends with DP_ERR_TIMEOUT and zeroed outputs.  0 turns it off; other plans
+ * and other kernels ignore it.  DP_ERR_INVALID_ARG outside [0, 1e6]. */
+dp_status dp_debug_stall(dp_plan_t plan, int microseconds);
+
 /* Wait for the plan's stream and copy the per-subcarrier status of the last
  * call that wrote it into host_status[n_sc] (host memory; may be NULL).
  * Returns the first non-DP_OK entry (DP_OK if all succeeded). */
@@ -202,7 +225,15 @@ dp_status dp_status_get(dp_plan_t plan, int *host_status);
  *   instance, instance after instance, into host_status (sum of n_sc entries;
  *   NULL allowed) and returns the first failure.
  * dp_batch_describe: a JSON string (owned by the batch) with the buckets,
- *   their work items and the chosen CTAs per SM. */
+ *   their work items, systems, algorithmic bytes (every system's H and X
+ *   rows and the symbols it reads, once each) and the chosen CTAs per SM.
+ * dp_batch_set_timing: mode 1 records a CUDA event before every bucket launch
+ *   and one after the last, inside the graph; mode 2 does the same with
+ *   eager launches (no graph); 0 turns it off.  Synchronizes the stream and
+ *   rebuilds the graph.
+ * dp_batch_bucket_ms: waits for the stream, then writes the device time of
+ *   each bucket of the last call (in describe's order, n entries at most)
+ *   into ms (host).  DP_ERR_UNSUPPORTED when timing is off. */
 typedef struct dp_batch *dp_batch_t;
 dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, dp_batch_t *out);
 dp_status dp_batch_destroy(dp_batch_t b);
@@ -212,6 +243,8 @@ dp_status dp_batch_tune(dp_batch_t b, const void *const *H, const void *const *S
                         int trials);
 dp_status dp_batch_status_get(dp_batch_t b, int *host_status);
 const char *dp_batch_describe(dp_batch_t b);
+dp_status dp_batch_set_timing(dp_batch_t b, int mode);
+dp_status dp_batch_bucket_ms(dp_batch_t b, float *ms, int n);
 
 /* ---- Continuous-batching server -------------------------------------------
  * Serving form of the precoder: a cell is one channel (its dp_plan_desc with
@@ -295,9 +328,11 @@ dp_status dp_server_reset_stats(dp_server_t s);
  * start-up, a real-time slot loop where an allocation's latency or implicit
  * synchronization would break the slot deadline, or code that runs while
  * the caller's allocator is locked.  It runs the streaming form of
- * dp_precode (Gram with the cluster sum, solve, apply; FP32) with all of its
- * workspace in one static device array of DP_NOALLOC_SCRATCH_BYTES that every
- * GPU loading the library reserves until the process exits.  No plan is
+ * dp_precode (Gram with the cluster sum, solve, apply; FP32; FD-WF clusters
+ * with B_c < U and B_c <= 32 in the B_c x B_c form of Sec. III-D, as
+ * dp_precode does) with all of its workspace in one static device array of
+ * DP_NOALLOC_SCRATCH_BYTES that every GPU loading the library reserves until
+ * the process exits.  No plan is
  * needed and nothing is allocated: the caller passes the description (as for
  * dp_plan_create; prec must be DP_FP32, refine 0), the stream, and the device
  * arrays H [n_sc][B][U], S [n_sc][K][U], X [n_sc][K][B] in the layouts above.
@@ -306,8 +341,11 @@ dp_status dp_server_reset_stats(dp_server_t s);
  * n_sys = n_sc (WF/ZF) or n_sc C (FD-WF); a larger problem returns
  * DP_ERR_UNSUPPORTED before anything is enqueued.
  * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  All calls on a device share the array and each call
+ * device current (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture, and do not use
+ * the entry point after a cudaDeviceReset of that device (the kept address
+ * belongs to the old context).  The cluster offsets reach the device as
+ * kernel parameters: the call copies nothing from host memory.  All calls on a device share the array and each call
  * overwrites what it reads, so calls whose work overlaps on the GPU race:
  * serialize them (one stream, or events).  host_status: NULL to return after
  * enqueueing; otherwise the call waits for the stream and writes the

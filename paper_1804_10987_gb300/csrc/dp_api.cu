@@ -21,6 +21,7 @@ struct dp_plan {
   int *d_off = nullptr;     // [C + 1]
   int *d_status = nullptr;  // [n_sc * nsys]: status of every system of the last call
   int nsys = 1;
+  int dbg_stall_us = 0;  // failure injection for tests (dp_debug_stall)
   // FD-WF clusters with B_c < U (<= 32) run the B_c x B_c form
   bool has_small = false, all_small = false;
   int bcp = 0;
@@ -71,8 +72,9 @@ dp::SysDesc make_sys(const dp_plan *p, bool per_cluster, const void *H) {
       break;
   }
   s.tma_ok = (p->d.U % 2 == 0) && (H == nullptr || aligned16(H));
-  s.refine = p->d.refine != 0 && p->d.prec != DP_FP32;
+  s.refine = dp::refine_mode(p->d.refine, p->d.prec == DP_FP32, p->d.mode == DP_MRT);
   s.mrt = p->d.mode == DP_MRT;
+  s.dbg_stall_us = p->dbg_stall_us;
   return s;
 }
 
@@ -192,10 +194,9 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
   if (!(d.rho2 > 0.f) || !std::isfinite(d.rho2) || !(d.Es > 0.f) || !std::isfinite(d.Es) ||
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
     return DP_ERR_INVALID_ARG;
-  if (d.refine != 0 && d.refine != 1) return DP_ERR_INVALID_ARG;
-  // The tensor-core path covers up to 64 users, its refinement step up to 32.
+  if (!dp::refine_valid(d.refine)) return DP_ERR_INVALID_ARG;
+  // The tensor-core path covers up to 64 users.
   if (d.prec != DP_FP32 && !dp::tc_supported(dp::padded_users(d.U))) return DP_ERR_UNSUPPORTED;
-  if (d.refine && d.prec != DP_FP32 && dp::padded_users(d.U) > 32) return DP_ERR_UNSUPPORTED;
 
   std::vector<int> sizes(d.C);
   if (d.cluster_sizes) {
@@ -353,9 +354,17 @@ cudaError_t precode_range(dp_plan *p, const float2 *h, const float2 *sy, float2 
     e = dp::launch_fd_small(dp::InstDesc{sd, h, sy, x, status, nullptr}, p->bcp, p->stream);
     if (e != cudaSuccess || p->all_small) return e;
   }
-  if (p->d.prec != DP_FP32 && dp::pipe_tc_supported(sd, p->UP))
-    return dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
-                              p->stream);
+  if (p->d.prec != DP_FP32 && dp::pipe_tc_supported(sd, p->UP)) {
+    e = dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
+                           p->stream);
+    if (e != cudaSuccess || sd.refine != 2) return e;
+    // automatic refinement: the group kernel redoes the groups whose systems
+    // the warp-specialized kernel marked (its other CTAs exit at once)
+    dp::SysDesc fx = sd;
+    fx.fixup = 1;
+    return dp::launch_fused_tc(fx, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
+                               p->stream);
+  }
   if (p->d.prec != DP_FP32)
     return dp::launch_fused_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
                                p->stream);
@@ -436,6 +445,12 @@ dp_status dp_precode_host(dp_plan_t p, const void *H, const void *S, void *X, in
   for (int i = nchunks - dp_plan::NSTAGE; i < nchunks && e == cudaSuccess; ++i)
     if (i >= 0) e = cudaStreamWaitEvent(p->stream, p->hp_down_done[i % dp_plan::NSTAGE], 0);
   return e == cudaErrorMemoryAllocation ? DP_ERR_OOM : cuda_status(e);
+}
+
+dp_status dp_debug_stall(dp_plan_t p, int microseconds) {
+  if (!p || microseconds < 0 || microseconds > 1000000) return DP_ERR_INVALID_ARG;
+  p->dbg_stall_us = microseconds;
+  return DP_OK;
 }
 
 dp_status dp_status_get(dp_plan_t p, int *host_status) {

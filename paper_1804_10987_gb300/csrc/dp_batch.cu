@@ -26,7 +26,7 @@
 
 namespace {
 
-enum Family { FAM_TC = 0, FAM_FUSED = 1, FAM_STREAM = 2, FAM_FDSMALL = 3 };
+enum Family { FAM_TC = 0, FAM_FUSED = 1, FAM_STREAM = 2, FAM_FDSMALL = 3, FAM_PIPE = 4 };
 
 struct Bucket {
   int family;
@@ -39,6 +39,15 @@ struct Bucket {
   int max_blocks = 1;   // occupancy limit per SM
   int blocks = 1;       // chosen CTAs per SM
   float tuned_ms = -1.f;
+  long long systems = 0;    // systems of the bucket's items
+  double alg_bytes = 0.0;   // algorithmic bytes: H rows, their X rows and the
+                            // system's symbols, once each
+  // warp-specialized family with automatic refinement: the list of groups
+  // holding marked systems (items ints, then the count) and the CTAs per SM
+  // of its fix-up launch
+  bool fix = false;
+  int *d_fix = nullptr;
+  int fix_blocks = 1;
 };
 
 struct Inst {
@@ -67,8 +76,7 @@ dp_status validate(const dp_plan_desc &d, std::vector<int> &off) {
   if (!(d.rho2 > 0.f) || !std::isfinite(d.rho2) || !(d.Es > 0.f) || !std::isfinite(d.Es) ||
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
     return DP_ERR_INVALID_ARG;
-  if (d.refine != 0 && d.refine != 1) return DP_ERR_INVALID_ARG;
-  if (d.refine && d.prec != DP_FP32 && dp::padded_users(d.U) > 32) return DP_ERR_UNSUPPORTED;
+  if (!dp::refine_valid(d.refine)) return DP_ERR_INVALID_ARG;
   off.assign(d.C + 1, 0);
   for (int c = 0; c < d.C; ++c) {
     int bc;
@@ -114,7 +122,7 @@ dp::SysDesc sys_of(const Inst &in, const void *H) {
   }
   s.tma_ok = (d.U % 2 == 0) && (H == nullptr || a16(H));
   s.skip_small = in.has_small ? 1 : 0;
-  s.refine = d.refine != 0 && d.prec != DP_FP32;
+  s.refine = dp::refine_mode(d.refine, d.prec == DP_FP32, d.mode == DP_MRT);
   s.mrt = d.mode == DP_MRT;
   return s;
 }
@@ -135,14 +143,22 @@ struct dp_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::string info;
+  // per-bucket timing (dp_batch_set_timing): event k before bucket k, the
+  // last after every bucket; 1 = recorded from the graph, 2 = eager launches
+  int timing = 0;
+  std::vector<cudaEvent_t> ev;
 };
 
 namespace {
 
 void free_batch(dp_batch *b) {
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (auto &bk : b->buckets) cudaFree(bk.d_items);
+  for (auto &bk : b->buckets) {
+    cudaFree(bk.d_items);
+    cudaFree(bk.d_fix);
+  }
   for (auto &in : b->insts) {
     cudaFree(in.w_G);
     cudaFree(in.w_Z);
@@ -162,7 +178,19 @@ cudaError_t enqueue_bucket(dp_batch *b, int k, cudaStream_t s) {
   if (bk.items.empty()) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(b->d_queues + k, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  const int grid = std::max(1, std::min<int>(bk.blocks * b->n_sm, (int)bk.items.size()));
+  const int n = (int)bk.items.size();
+  const int grid = std::max(1, std::min<int>(bk.blocks * b->n_sm, n));
+  if (bk.family == FAM_PIPE) {
+    if (bk.fix && (e = cudaMemsetAsync(bk.d_fix + n, 0, sizeof(int), s)) != cudaSuccess) return e;
+    e = dp::launch_batch_pipe_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n,
+                                 bk.fix ? bk.d_fix : nullptr, bk.fix ? bk.d_fix + n : nullptr,
+                                 std::min(b->n_sm, n), s);
+    if (e != cudaSuccess || !bk.fix) return e;
+    // automatic refinement: the group kernel redoes the listed groups
+    return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, b->d_queues + k,
+                               bk.Kmax, std::max(1, bk.fix_blocks * b->n_sm), s, bk.d_fix,
+                               bk.d_fix + n);
+  }
   if (bk.family == FAM_TC)
     return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, (int)bk.items.size(),
                                b->d_queues + k, bk.Kmax, grid, s);
@@ -190,9 +218,16 @@ cudaError_t enqueue_streaming(dp_batch *b, int i, cudaStream_t s) {
 
 // The persistent bucket launches (the part a graph captures: they read every
 // pointer from the device table, so the graph is independent of the call).
-cudaError_t enqueue_buckets(dp_batch *b, cudaStream_t s) {
+cudaError_t enqueue_buckets(dp_batch *b, cudaStream_t s, bool capturing = false) {
   cudaError_t e = cudaSuccess;
-  for (size_t k = 0; k < b->buckets.size() && e == cudaSuccess; ++k) e = enqueue_bucket(b, (int)k, s);
+  const bool ev = b->timing != 0 && b->ev.size() == b->buckets.size() + 1;
+  // inside a capture the records become event-record nodes of the graph
+  const unsigned fl = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  for (size_t k = 0; k < b->buckets.size() && e == cudaSuccess; ++k) {
+    if (ev) e = cudaEventRecordWithFlags(b->ev[k], s, fl);
+    if (e == cudaSuccess) e = enqueue_bucket(b, (int)k, s);
+  }
+  if (ev && e == cudaSuccess) e = cudaEventRecordWithFlags(b->ev[b->buckets.size()], s, fl);
   return e;
 }
 
@@ -235,12 +270,14 @@ dp_status build_graph(dp_batch *b) {
     cudaGraphDestroy(b->graph);
     b->graph = nullptr;
   }
-  if (b->stream == nullptr) return DP_OK;  // the legacy stream cannot be captured: run eagerly
+  // the legacy stream cannot be captured, and timing mode 2 asks for eager
+  // launches: run eagerly
+  if (b->stream == nullptr || b->timing == 2) return DP_OK;
   if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
     cudaGetLastError();
     return DP_OK;
   }
-  cudaError_t e = enqueue_buckets(b, b->stream);
+  cudaError_t e = enqueue_buckets(b, b->stream, true);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
   if (e != cudaSuccess || e2 != cudaSuccess || !g) {
@@ -265,11 +302,14 @@ void describe(dp_batch *b) {
     char buf[256];
     std::snprintf(buf, sizeof buf,
                   "%s{\"family\": \"%s\", \"users_padded\": %d, \"items\": %zu, "
+                  "\"systems\": %lld, \"alg_bytes\": %.0f, "
                   "\"ctas_per_sm\": %d, \"max_ctas_per_sm\": %d, \"tuned_ms\": %.4f}",
                   k ? ", " : "",
                   bk.family == FAM_TC ? (bk.bf16 ? "tc_bf16" : "tc_fp16")
+                  : bk.family == FAM_PIPE ? (bk.bf16 ? "tc_pipe_bf16" : "tc_pipe_fp16")
                   : bk.family == FAM_FDSMALL ? "fd_small_clusters" : "fp32_fused", bk.UP,
-                  bk.items.size(), bk.blocks, bk.max_blocks, bk.tuned_ms);
+                  bk.items.size(), bk.systems, bk.alg_bytes, bk.blocks, bk.max_blocks,
+                  bk.tuned_ms);
     s += buf;
   }
   char tail[64];
@@ -344,7 +384,8 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
       in.all_small = nsmall == in.d.C;
       in.bcp = dp::fd_small_bcp(maxsmall);
     }
-    if (in.d.prec != DP_FP32 && dp::tc_supported(in.UP)) in.family = FAM_TC;
+    if (in.d.prec != DP_FP32 && dp::tc_supported(in.UP))
+      in.family = dp::pipe_tc_supported(sys_of(in, nullptr), in.UP) ? FAM_PIPE : FAM_TC;
     else if (dp::fused_smem_bytes(in.UP, in.maxrows, in.d.K) != 0) in.family = FAM_FUSED;
     else in.family = FAM_STREAM;
     in.status_off = status_len;
@@ -401,7 +442,8 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
             cudaMalloc(&in.w_scale, sizeof(float) * nsys_total) != cudaSuccess;
       continue;
     }
-    auto key = std::make_tuple(in.family, in.UP, in.family == FAM_TC ? (int)in.bf16 : 0);
+    const bool tcfam = in.family == FAM_TC || in.family == FAM_PIPE;
+    auto key = std::make_tuple(in.family, in.UP, tcfam ? (int)in.bf16 : 0);
     auto it = bucket_of.find(key);
     int k;
     if (it == bucket_of.end()) {
@@ -410,7 +452,7 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
       Bucket bk;
       bk.family = in.family;
       bk.UP = in.UP;
-      bk.bf16 = in.family == FAM_TC && in.bf16;
+      bk.bf16 = tcfam && in.bf16;
       b->buckets.push_back(bk);
     } else {
       k = it->second;
@@ -418,13 +460,31 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
     Bucket &bk = b->buckets[k];
     bk.Kmax = std::max(bk.Kmax, in.d.K);
     bk.maxrows = std::max(bk.maxrows, in.maxrows);
-    const int per = in.family == FAM_TC ? dp::tc_systems_per_group(in.UP) : 1;
+    if (in.family == FAM_PIPE && sys_of(in, nullptr).refine == 2) bk.fix = true;
+    const int per = in.family == FAM_TC   ? dp::tc_systems_per_group(in.UP)
+                    : in.family == FAM_PIPE ? dp::pipe_systems_per_group(in.UP)
+                                            : 1;
     for (int s0 = 0; s0 < nsys_total; s0 += per)
       bk.items.push_back(dp::WorkItem{i, s0, std::min(per, nsys_total - s0)});
   }
   if (oom) {
     free_batch(b);
     return DP_ERR_OOM;
+  }
+  // algorithmic bytes per bucket: every system's H rows and X rows, and the
+  // symbols it reads (per cluster in FD-WF, which hands s to every cluster)
+  for (auto &bk : b->buckets) {
+    for (const dp::WorkItem &w : bk.items) {
+      const Inst &in = b->insts[w.inst];
+      for (int j = 0; j < w.nact; ++j) {
+        const int sys = w.sys0 + j;
+        const int c = sys % in.nsys;
+        const int rows = in.nsys == 1 ? in.d.B : in.off[c + 1] - in.off[c];
+        bk.alg_bytes += 8.0 * ((double)in.d.U * rows + (double)in.d.K * rows +
+                               (double)in.d.K * in.d.U);
+        ++bk.systems;
+      }
+    }
   }
   // largest items first (antenna rows of the item's systems), so that the
   // queue's tail is made of small items
@@ -443,9 +503,19 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
                cudaMemcpyHostToDevice);
     bk.max_blocks = bk.family == FAM_TC
                         ? dp::tc_max_blocks_per_sm(bk.UP, bk.bf16, bk.Kmax)
+                        : bk.family == FAM_PIPE ? 1  // one warp-specialized CTA per SM
                         : bk.family == FAM_FDSMALL
                               ? dp::fd_small_max_blocks_per_sm(bk.UP, bk.Kmax)
                               : dp::fused_max_blocks_per_sm(bk.UP, bk.maxrows, bk.Kmax);
+    if (bk.fix) {
+      bk.fix_blocks = dp::tc_max_blocks_per_sm(bk.UP, bk.bf16, bk.Kmax);
+      if (bk.fix_blocks < 1 ||
+          cudaMalloc(&bk.d_fix, sizeof(int) * (bk.items.size() + 1)) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return bk.fix_blocks < 1 ? DP_ERR_UNSUPPORTED : DP_ERR_OOM;
+      }
+    }
     if (bk.max_blocks < 1) {
       free_batch(b);
       return DP_ERR_UNSUPPORTED;
@@ -526,6 +596,38 @@ dp_status dp_batch_tune(dp_batch_t b, const void *const *H, const void *const *S
   if (rc != DP_OK) return rc;
   describe(b);
   return build_graph(b);
+}
+
+dp_status dp_batch_set_timing(dp_batch_t b, int mode) {
+  if (!b || mode < 0 || mode > 2) return DP_ERR_INVALID_ARG;
+  if (cudaSetDevice(b->device) != cudaSuccess) return DP_ERR_CUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DP_ERR_CUDA;
+  if (mode != 0 && b->ev.empty()) {
+    b->ev.assign(b->buckets.size() + 1, nullptr);
+    for (auto &e : b->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return DP_ERR_CUDA;
+      }
+  }
+  b->timing = mode;
+  return build_graph(b);
+}
+
+dp_status dp_batch_bucket_ms(dp_batch_t b, float *ms, int n) {
+  if (!b || !ms || n < 0) return DP_ERR_INVALID_ARG;
+  if (b->timing == 0 || b->ev.size() != b->buckets.size() + 1) return DP_ERR_UNSUPPORTED;
+  if (cudaSetDevice(b->device) != cudaSuccess) return DP_ERR_CUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return DP_ERR_CUDA;
+  for (int k = 0; k < n && k < (int)b->buckets.size(); ++k) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, b->ev[k], b->ev[k + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      return DP_ERR_CUDA;
+    }
+    ms[k] = t;
+  }
+  return DP_OK;
 }
 
 const char *dp_batch_describe(dp_batch_t b) { return b ? b->info.c_str() : ""; }

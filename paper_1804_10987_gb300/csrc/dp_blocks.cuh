@@ -17,6 +17,12 @@ constexpr int NT = 256;  // threads per CTA of the per-system kernels
 // while its subtraction amplifies rounding errors by at most 1 / (1 - 0.875)
 // = 8; beyond that t is formed as tr(T G T).
 constexpr float kLemmaMaxRatio = 0.875f;
+// The reduced-precision (BF16 / FP16 Gram) path keeps Lemma 1 up to an
+// amplification of 256: with FP32 sums of U <= 64 terms that bounds its
+// rounding contribution to t near 256 * 64 * 2^-24 ~ 1e-3 in the worst case
+// and ~1e-5 typically, against the same path's 1e-3 bar, where the 16-bit
+// Gram itself contributes ~1e-4.  Beyond it t is formed as tr(T G T).
+constexpr float kLemmaMaxRatioLP = 1.0f - 1.0f / 256.0f;
 
 constexpr int pow2_floor(int x) {
   int p = 1;
@@ -485,12 +491,24 @@ __device__ __forceinline__ int split_solve(float2 (&row)[UP / 2], const float2 *
                                            const float2 *Ss, float2 *zout, int ldz, float kappa,
                                            float rho2, float Es, int U, int K, int sl,
                                            bool finite_in, bool store, float &scale,
-                                           float &zmax, bool mrt = false) {
+                                           float &zmax, bool mrt = false,
+                                           float *sens = nullptr) {
   constexpr int HALF = UP / 2, SEG = 2 * UP;
   static_assert(SEG <= 32, "a system fits a warp");
   const int i = sl % UP, h = sl / UP;
   int st = finite_in ? ST_OK : ST_NONFINITE;
   bool bad = false;
+  // ||G||_F^2 from A = G + kappa I (for the sensitivity estimate)
+  float g2 = 0.f;
+  if (sens && i < U) {
+#pragma unroll
+    for (int jj = 0; jj < HALF; ++jj) {
+      const int j = h * HALF + jj;
+      const float re = row[jj].x - (j == i ? kappa : 0.f);
+      if (j < U) g2 = fmaf(re, re, fmaf(row[jj].y, row[jj].y, g2));
+    }
+  }
+  if (sens) g2 = seg_sum<SEG>(g2);
   // MRT (kappa = 0, no inverse): t = tr(G), z = s; row keeps G
 #pragma unroll
   for (int p = 0; p < UP; ++p) {
@@ -533,6 +551,9 @@ __device__ __forceinline__ int split_solve(float2 (&row)[UP / 2], const float2 *
       fr = 0.f;
     }
     const float tr = seg_sum<SEG>(dg), fro = seg_sum<SEG>(fr);
+    // sensitivity of z to a relative perturbation of G: ||G|| ||A^{-1}||,
+    // estimated as ||G||_F ||T||_F / U
+    if (sens) *sens = (mrt || st != ST_OK || bad) ? 0.f : sqrtf(g2 * fro) / (float)U;
     float t = mrt ? tr : tr - kappa * fro;
     const bool need = !mrt && kappa * fro > kLemmaMaxRatio * tr;
     if (__any_sync(FULL, need && st == ST_OK)) {
@@ -623,7 +644,7 @@ __device__ __forceinline__ bool warp_gj_inverse(float2 (&row)[UP], int lane, int
 template <int UP>
 __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int ldz, float kappa,
                           float rho2, float Es, int U, int K, int lane, bool finite_in,
-                          float &scale, bool mrt = false) {
+                          float &scale, bool mrt = false, float *sens = nullptr) {
   if constexpr (2 * UP <= 32) {  // split rows over 2 UP lanes
     constexpr int HALF = UP / 2, SEG = 2 * UP;
     const int sl = lane % SEG, i = sl % UP, h = sl / UP;
@@ -636,7 +657,7 @@ __device__ int warp_solve(const float2 *Gs, const float2 *Ss, float2 *zout, int 
     }
     float zm;
     return split_solve<UP>(row, Gs, Ss, zout, ldz, kappa, rho2, Es, U, K, sl, finite_in,
-                           lane < SEG, scale, zm, mrt);
+                           lane < SEG, scale, zm, mrt, sens);
   }
   float2 row[UP];
 #pragma unroll

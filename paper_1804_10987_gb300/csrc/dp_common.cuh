@@ -14,7 +14,19 @@ enum : int {
   ST_NOT_PD = 6,
   ST_NONFINITE = 7,
   ST_TIMEOUT = 8,
+  // internal, never returned: the warp-specialized kernel's mark of a system
+  // that the automatic refinement wants; its fix-up launch replaces it
+  ST_REFINE = 100,
 };
+
+// Automatic precision escalation (reduced-precision path): a system is
+// flagged when eps * sens >= kRefineTrigger, with eps the unit roundoff of the
+// Gram's 16-bit type (2^-8 BF16, 2^-11 FP16) and sens = ||G||_F ||T||_F / U
+// the sensitivity of z to a relative perturbation of G.  The worst relative
+// error of the unflagged outputs measured about 0.25 eps sens, so the trigger
+// keeps them near 5e-4, half the reduced-precision bar; a flagged system's
+// Gram is recomputed in FP32.
+constexpr float kRefineTrigger = 2e-3f;
 
 constexpr unsigned FULL = 0xffffffffu;
 // Iteration bound of every spin on an mbarrier.  After a few immediate
@@ -113,6 +125,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   return false;
 }
 
+// The same bounded wait, which also gives up as soon as *abort_f is set (a
+// role of a warp-specialized kernel whose partner role gave up).  Waits that
+// guard the kernel's exit -- its own copies and MMAs landing before the CTA
+// leaves or frees TMEM -- use mbar_wait, never this form.
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity,
+                                             const volatile int *abort_f) {
+  for (uint32_t i = 0; i < kWaitIters; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_f) return false;
+    if (i >= kSpinBeforeSleep) __nanosleep(64);
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // CTA-wide wait: one thread polls the barrier, the others park at the CTA
 // barrier (no issue slots spent spinning).  Returns false on timeout, the
 // same value in every thread.
@@ -138,8 +170,14 @@ struct SysDesc {
   int tma_ok;       // rows may be fetched with 1-D bulk copies
   int skip_small;   // FD-WF: systems with fewer antennas than users (and at
                     // most 32) are left to the B_c x B_c kernel
-  int refine;       // tensor-core path: one step of iterative refinement of z
+  int refine;       // tensor-core path, one step of iterative refinement of z:
+                    // 0 never, 1 every system, 2 systems the trigger flags
   int mrt;          // maximum ratio transmission: no inverse, z = s, t = tr(G)
+  int fixup;        // k_fused_tc: only groups holding ST_REFINE systems (the
+                    // automatic refinement after the warp-specialized kernel)
+  int dbg_stall_us; // failure injection (tests): the warp-specialized kernel's
+                    // MMA issuer first waits this long on a flag that nothing
+                    // sets, then gives up as a timed-out wait does; 0: off
 };
 
 // One precoding instance: its systems and its device arrays (H [n_sc][B][U],

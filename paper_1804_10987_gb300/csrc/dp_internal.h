@@ -11,6 +11,15 @@ namespace dp {
 // Users padded to the kernels' granularity (a multiple of 8, at most 64).
 inline int padded_users(int U) { return ((U + 7) / 8) * 8; }
 
+// SysDesc::refine from a description's refine field (-1 none, 0 automatic,
+// 1 every system) and its precision / mode: refinement concerns the 16-bit
+// Gram of the tensor-core path, and MRT has nothing to refine.
+inline int refine_mode(int refine, bool fp32, bool mrt) {
+  if (fp32 || mrt) return 0;
+  return refine == 1 ? 1 : (refine == 0 ? 2 : 0);
+}
+inline bool refine_valid(int refine) { return refine >= -1 && refine <= 1; }
+
 // CTAs of `kernel` (launched with `threads` threads and `dyn_bytes` of dynamic
 // shared memory, each holding `tmem_cols` TMEM columns) that one SM holds at
 // once, from the limits themselves: threads, registers (allocated per warp in
@@ -24,6 +33,35 @@ int stream_chunk_rows(int UP);
 // Dynamic shared memory of the fused kernel for systems of up to maxrows
 // antennas; 0 if it cannot fit in one CTA.
 size_t fused_smem_bytes(int UP, int maxrows, int K);
+
+// The FP32 path's launchers for one padded user count (defined in
+// dp_fp32_impl.cuh, instantiated in dp_fp32_u*.cu).
+template <int UP>
+struct Fp32Ops {
+  static cudaError_t gram(const SysDesc &d, const float2 *H, float2 *Gout, cudaStream_t s);
+  static cudaError_t solve(const SysDesc &d, const float2 *Gin, const float2 *S, float2 *Z,
+                           float *scale, int *status, cudaStream_t s);
+  static cudaError_t apply(const SysDesc &d, const float2 *H, const float2 *Z, const float *scale,
+                           float2 *X, cudaStream_t s);
+  static cudaError_t fused(const SysDesc &d, int maxrows, const float2 *H, const float2 *S,
+                           float2 *X, int *status, float *scale_out, cudaStream_t s);
+  static cudaError_t batch_fused(const InstDesc *insts, const WorkItem *items, int n_items,
+                                 int *queue, int maxrows, int Kmax, int grid, cudaStream_t s);
+  static int blocks(int maxrows, int Kmax);
+  static size_t fused_bytes(int maxrows, int K);
+};
+
+// The tensor-core group kernel's launchers for one padded user count
+// (defined in dp_tc_impl.cuh, instantiated in dp_tc_u*.cu).
+template <int UP>
+struct TcOps {
+  static cudaError_t fused(const SysDesc &d, bool bf16, const float2 *H, const float2 *S,
+                           float2 *X, int *status, float *scale_out, cudaStream_t s);
+  static cudaError_t batch(bool bf16, const InstDesc *insts, const WorkItem *items, int n_items,
+                           int *queue, int Kmax, int grid, cudaStream_t s, const int *fix_list,
+                           const int *fix_count);
+  static int blocks(bool bf16, int Kmax);
+};
 
 cudaError_t launch_gram(const SysDesc &d, int UP, const float2 *H, float2 *Gout,
                         cudaStream_t s);
@@ -47,14 +85,26 @@ cudaError_t launch_fused_tc(const SysDesc &d, int UP, bool bf16, const float2 *H
 // Systems per work item of the tensor-core path (the CTA's group).
 int tc_systems_per_group(int UP);
 // Persistent tensor-core kernel over a work-item queue (queue must be 0).
+// With fix_count non-NULL it takes only items[fix_list[i]], i < *fix_count
+// (the fix-up after the warp-specialized kernel; its CTAs exit at once when
+// the count is 0).
 cudaError_t launch_batch_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
-                            int n_items, int *queue, int Kmax, int grid, cudaStream_t s);
+                            int n_items, int *queue, int Kmax, int grid, cudaStream_t s,
+                            const int *fix_list = nullptr, const int *fix_count = nullptr);
 int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax);
 // Warp-specialized persistent form of the same arithmetic (bit-identical),
 // for users padded to 8 or 16, 1 <= K <= 16 and bulk-copyable rows.
 bool pipe_tc_supported(const SysDesc &d, int UP);
 cudaError_t launch_pipe_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
                            float2 *X, int *status, float *scale_out, cudaStream_t s);
+// The same kernel over a batch bucket's work items (groups of up to
+// pipe_systems_per_group(UP) systems of one instance), one CTA per SM (grid);
+// with automatic refinement the groups holding marked systems are appended
+// to fix_list (counter fix_count, zeroed before the launch).
+int pipe_systems_per_group(int UP);
+cudaError_t launch_batch_pipe_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
+                                 int n_items, int *fix_list, int *fix_count, int grid,
+                                 cudaStream_t s);
 
 // FD-WF clusters with B_c < U (and B_c <= 32) in the B_c x B_c form:
 // padded cluster width (8, 16, 32; 0 if none fits) and the launchers.

@@ -8,6 +8,7 @@
 // it: a call overwrites everything it reads before reading it, so nothing has
 // to start at zero, but two calls whose work overlaps on the GPU (different
 // streams, or different host threads without ordering) race on it.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -27,7 +28,9 @@ unsigned char *g_addr[kMaxDevices] = {};
 
 // Device address of g_scratch on device dev (the current device).  In host
 // code the symbol names a host-side stand-in, so the address is looked up
-// once per device with that device current and cached.
+// once per device with that device current and cached for the life of the
+// process (keyed on the device ordinal only: a cudaDeviceReset, which gives
+// the device a new context, leaves the cached address stale).
 dp_status scratch_on(int dev, unsigned char **out) {
   if (dev < 0 || dev >= kMaxDevices) return DP_ERR_UNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -44,6 +47,17 @@ dp_status scratch_on(int dev, unsigned char **out) {
 }
 
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Cluster offsets passed by value (kernel parameters): the device copy is
+// written by a kernel, so no host buffer (pageable or pinned) is involved.
+constexpr int kOffChunk = 512;
+struct OffChunk {
+  int first, n;
+  int v[kOffChunk];
+};
+__global__ void k_fill_offsets(OffChunk c, int *dst) {
+  for (int i = threadIdx.x; i < c.n; i += blockDim.x) dst[c.first + i] = c.v[i];
+}
 bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 }  // namespace
@@ -114,9 +128,15 @@ extern "C" dp_status dp_precode_noalloc(const dp_plan_desc *desc, dp_stream_t st
   float *w_sc = reinterpret_cast<float *>(base + b_off + b_st + b_G + b_Z);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 
-  // Pageable source: the copy is staged before the call returns.
-  cudaError_t e = cudaMemcpyAsync(w_off, off.data(), sizeof(int) * (d.C + 1),
-                                  cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaSuccess;
+  for (int first = 0; first <= d.C && e == cudaSuccess; first += kOffChunk) {
+    OffChunk c{};
+    c.first = first;
+    c.n = std::min(kOffChunk, d.C + 1 - first);
+    for (int i = 0; i < c.n; ++i) c.v[i] = off[first + i];
+    k_fill_offsets<<<1, 128, 0, st>>>(c, w_off);
+    e = cudaGetLastError();
+  }
 
   dp::SysDesc sd{};
   sd.U = d.U;
@@ -141,11 +161,31 @@ extern "C" dp_status dp_precode_noalloc(const dp_plan_desc *desc, dp_stream_t st
   sd.mrt = d.mode == DP_MRT;
   const int UP = dp::padded_users(d.U);
   const float2 *h = static_cast<const float2 *>(H);
-  if (e == cudaSuccess) e = dp::launch_gram(sd, UP, h, w_G, st);
-  if (e == cudaSuccess)
-    e = dp::launch_solve(sd, UP, w_G, static_cast<const float2 *>(S), w_Z, w_sc, w_st, st);
-  if (e == cudaSuccess && !k0)
-    e = dp::launch_apply(sd, UP, h, w_Z, w_sc, static_cast<float2 *>(X), st);
+  // FD-WF clusters with fewer antennas than users (at most 32) take the
+  // paper's B_c x B_c form, as in dp_precode; it needs no workspace
+  int maxsmall = 0, nsmall = 0;
+  if (fd)
+    for (int c = 0; c < d.C; ++c) {
+      const int bc = off[c + 1] - off[c];
+      if (bc < d.U && bc <= 32) {
+        ++nsmall;
+        maxsmall = std::max(maxsmall, bc);
+      }
+    }
+  if (nsmall > 0) {
+    sd.skip_small = 1;
+    if (e == cudaSuccess)
+      e = dp::launch_fd_small(dp::InstDesc{sd, h, static_cast<const float2 *>(S),
+                                           static_cast<float2 *>(X), w_st, nullptr},
+                              dp::fd_small_bcp(maxsmall), st);
+  }
+  if (nsmall < (fd ? d.C : 1)) {
+    if (e == cudaSuccess) e = dp::launch_gram(sd, UP, h, w_G, st);
+    if (e == cudaSuccess)
+      e = dp::launch_solve(sd, UP, w_G, static_cast<const float2 *>(S), w_Z, w_sc, w_st, st);
+    if (e == cudaSuccess && !k0)
+      e = dp::launch_apply(sd, UP, h, w_Z, w_sc, static_cast<float2 *>(X), st);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return DP_ERR_CUDA;

@@ -189,7 +189,7 @@ dp::SysDesc sys_of(const Cell &c, const void *H) {
   }
   s.tma_ok = (d.U % 2 == 0) && a16(H);
   s.skip_small = c.has_small ? 1 : 0;
-  s.refine = d.refine != 0 && d.prec != DP_FP32;
+  s.refine = dp::refine_mode(d.refine, d.prec == DP_FP32, d.mode == DP_MRT);
   s.mrt = d.mode == DP_MRT;
   return s;
 }
@@ -402,10 +402,9 @@ dp_status dp_server_add_cell(dp_server_t sv, const dp_plan_desc *desc, const voi
   const dp_plan_desc &d = *desc;
   if (d.U < 1 || d.U > 64 || d.B < 1 || d.B > 4096 || d.C < 1 || d.C > d.B || d.n_sc < 1 ||
       d.K < 1 || d.K > 64 || (d.mode != DP_ZF && d.mode != DP_WF && d.mode != DP_FDWF && d.mode != DP_MRT) ||
-      (d.prec != DP_FP32 && d.prec != DP_BF16 && d.prec != DP_FP16) || (d.refine != 0 && d.refine != 1) ||
+      (d.prec != DP_FP32 && d.prec != DP_BF16 && d.prec != DP_FP16) || !dp::refine_valid(d.refine) ||
       !(d.rho2 > 0.f) || !(d.Es > 0.f) || !(d.N0 >= 0.f) || !(d.tau >= 0.f))
     return DP_ERR_INVALID_ARG;
-  if (d.refine && d.prec != DP_FP32 && dp::padded_users(d.U) > 32) return DP_ERR_UNSUPPORTED;
   Cell c;
   c.d = d;
   c.off.assign(d.C + 1, 0);

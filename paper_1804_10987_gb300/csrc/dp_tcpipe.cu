@@ -83,7 +83,7 @@ struct PpGeo {
   static constexpr int SZ = GS + NG * UP * UP * 8;              // s, then z: 2 x NG x [K][UP]
   static constexpr int INFO = SZ + 2 * NG * PP_KMAX * UP * 8;   // st, sc, zexp: 2 x NG each
   static constexpr int BARS = INFO + 3 * 2 * NG * 4;
-  static constexpr int MISC = BARS + B_COUNT * 8;               // tmem base, abort, per-warp done
+  static constexpr int MISC = BARS + B_COUNT * 8;               // tmem base, abort, stall flag, per-warp done
   static constexpr int BYTES = MISC + 48 + 1024;                // + alignment slack
   static_assert(NG % PP_SV == 0 && SPW >= 1, "whole systems per solver warp");
   static_assert((32 * PP_CV) % (NG * UP) == 0, "a converter thread's Gram items share a system");
@@ -113,15 +113,43 @@ __device__ __forceinline__ bool seg_all(bool v, int lane) {
   return (b & m) == m;
 }
 
+// Where a launch's groups come from: a single plan's systems taken NG at a
+// time (items == nullptr, instance in0), or a batch bucket's work items (an
+// instance and up to NG of its systems each).  Every role walks groups
+// blockIdx.x, blockIdx.x + gridDim.x, ... in the same order.
+struct PpSrc {
+  InstDesc in0;
+  const InstDesc *insts;
+  const WorkItem *items;
+  int n_groups;
+  int *fix_list;   // batch, automatic refinement: groups holding ST_REFINE
+  int *fix_count;  // systems, appended once per group by the solvers
+};
+struct PpGroup {
+  const InstDesc *in;
+  int sys0, nact;
+};
+template <int UP>
+__device__ __forceinline__ PpGroup pp_group(const PpSrc &src, int g) {
+  if (src.items) {
+    const WorkItem w = src.items[g];
+    return PpGroup{src.insts + w.inst, w.sys0, w.nact};
+  }
+  const int total = src.in0.d.n_sc * src.in0.d.nsys;
+  return PpGroup{&src.in0, g * PpGeo<UP>::NG, min(PpGeo<UP>::NG, total - g * PpGeo<UP>::NG)};
+}
+
 // A system of a group: subcarrier, first antenna, antennas; live = exists and
 // is not left to the B_c x B_c kernel.
 struct PpSys {
   int n, lo, nr;
   bool live;
 };
-__device__ __forceinline__ PpSys pp_sys(const SysDesc &d, int total, int sys) {
+__device__ __forceinline__ PpSys pp_sys(const PpGroup &G, int s) {
   PpSys r{0, 0, 0, false};
-  if (sys < total) {
+  if (s < G.nact) {
+    const SysDesc &d = G.in->d;
+    const int sys = G.sys0 + s;
     r.n = sys / d.nsys;
     int lo, hi;
     sys_rows(d, sys - r.n * d.nsys, lo, hi);
@@ -133,13 +161,13 @@ __device__ __forceinline__ PpSys pp_sys(const SysDesc &d, int total, int sys) {
   }
   return r;
 }
-// Largest antenna count over the live systems of group g (0: nothing to do;
+// Largest antenna count over the live systems of a group (0: nothing to do;
 // every role skips such a group).
 template <int UP>
-__device__ int pp_group_rows(const SysDesc &d, int total, int g) {
+__device__ int pp_group_rows(const PpGroup &G) {
   int m = 0;
   for (int s = 0; s < PpGeo<UP>::NG; ++s) {
-    const PpSys y = pp_sys(d, total, g * PpGeo<UP>::NG + s);
+    const PpSys y = pp_sys(G, s);
     if (y.live) m = max(m, y.nr);
   }
   return m;
@@ -147,17 +175,14 @@ __device__ int pp_group_rows(const SysDesc &d, int total, int g) {
 
 // ------------------------------------------------------------- producer ---
 template <int UP>
-__device__ void pp_producer(const InstDesc &in, int ngroups, unsigned char *base,
-                            uint64_t *bars, volatile int *abort_f) {
+__device__ void pp_producer(const PpSrc &src, unsigned char *base, uint64_t *bars,
+                            volatile int *abort_f) {
   using T = PpGeo<UP>;
-  const SysDesc &d = in.d;
-  const int total = d.n_sc * d.nsys;
-  const size_t rowb = (size_t)d.U * 8;
   uint32_t use = 0;
   bool ok = true;
   auto stage = [&](uint32_t bytes) -> unsigned char * {
     const int slot = use % PP_NRAW;
-    if (use >= PP_NRAW) ok = mbar_wait(&bars[B_RAWEMPTY + slot], ((use / PP_NRAW) - 1) & 1);
+    if (use >= PP_NRAW) ok = mbar_wait_ab(&bars[B_RAWEMPTY + slot], ((use / PP_NRAW) - 1) & 1, abort_f);
     if (ok && *abort_f) ok = false;
     if (!ok) return nullptr;
     mbar_arrive_expect_tx(&bars[B_RAWFULL + slot], bytes);
@@ -165,14 +190,17 @@ __device__ void pp_producer(const InstDesc &in, int ngroups, unsigned char *base
   };
   int prev = -1;
   for (int g = blockIdx.x; ok; g += gridDim.x) {
-    const bool have = g < ngroups;
-    const int rows = have ? pp_group_rows<UP>(d, total, g) : 0;
+    const bool have = g < src.n_groups;
+    const PpGroup G = have ? pp_group<UP>(src, g) : PpGroup{nullptr, 0, 0};
+    const int rows = have ? pp_group_rows<UP>(G) : 0;
     if (have && rows == 0) continue;
     if (have) {
+      const SysDesc &d = G.in->d;
+      const size_t rowb = (size_t)d.U * 8;
       for (int c = 0; c * PP_GCH < rows && ok; ++c) {
         uint32_t bytes = 0;
         for (int s = 0; s < T::NG; ++s) {
-          const PpSys y = pp_sys(d, total, g * T::NG + s);
+          const PpSys y = pp_sys(G, s);
           const int r = y.live ? min(PP_GCH, y.nr - c * PP_GCH) : 0;
           if (r > 0) bytes += (uint32_t)(r * rowb);
         }
@@ -180,25 +208,28 @@ __device__ void pp_producer(const InstDesc &in, int ngroups, unsigned char *base
         if (!dst) break;
         const uint64_t *bar = &bars[B_RAWFULL + use % PP_NRAW];
         for (int s = 0; s < T::NG; ++s) {
-          const PpSys y = pp_sys(d, total, g * T::NG + s);
+          const PpSys y = pp_sys(G, s);
           const int r = y.live ? min(PP_GCH, y.nr - c * PP_GCH) : 0;
           if (r > 0)
             tma_load_1d(dst + s * PP_GCH * rowb,
-                        in.H + ((size_t)y.n * d.B + y.lo + c * PP_GCH) * d.U, (uint32_t)(r * rowb),
-                        const_cast<uint64_t *>(bar));
+                        G.in->H + ((size_t)y.n * d.B + y.lo + c * PP_GCH) * d.U,
+                        (uint32_t)(r * rowb), const_cast<uint64_t *>(bar));
         }
         ++use;
       }
     }
     if (prev >= 0 && ok) {
+      const PpGroup P = pp_group<UP>(src, prev);
+      const SysDesc &d = P.in->d;
+      const size_t rowb = (size_t)d.U * 8;
       for (int s = 0; s < T::NG && ok; ++s) {
-        const PpSys y = pp_sys(d, total, prev * T::NG + s);
+        const PpSys y = pp_sys(P, s);
         if (!y.live) continue;
         for (int m0 = 0; m0 < y.nr && ok; m0 += PP_MT) {
           const int r = min(PP_MT, y.nr - m0);
           unsigned char *dst = stage((uint32_t)(r * rowb));
           if (!dst) break;
-          tma_load_1d(dst, in.H + ((size_t)y.n * d.B + y.lo + m0) * d.U, (uint32_t)(r * rowb),
+          tma_load_1d(dst, P.in->H + ((size_t)y.n * d.B + y.lo + m0) * d.U, (uint32_t)(r * rowb),
                       &bars[B_RAWFULL + use % PP_NRAW]);
           ++use;
         }
@@ -229,7 +260,7 @@ struct PpPend {  // an apply tile whose MMAs may be in flight
 // symbols 8 h .. 8 h + 7 (h = which of the two warps of the quarter).
 __device__ bool pp_readout(const PpPend &p, int K, int B, uint32_t taddr, uint64_t *bars,
                            volatile int *abort_f, int warp, int lane) {
-  bool w = mbar_wait(&bars[B_ACCDONE + p.at], (p.tile >> 1) & 1);
+  bool w = mbar_wait_ab(&bars[B_ACCDONE + p.at], (p.tile >> 1) & 1, abort_f);
   w = __all_sync(FULL, w) != 0;
   if (!w) {
     *abort_f = 1;
@@ -260,14 +291,10 @@ __device__ bool pp_readout(const PpPend &p, int K, int B, uint32_t taddr, uint64
 }
 
 template <int UP, bool BF16>
-__device__ void pp_converter(const InstDesc &in, int ngroups, unsigned char *base,
-                             uint64_t *bars, uint32_t taddr, volatile int *abort_f,
-                             volatile int *done_w) {
+__device__ void pp_converter(const PpSrc &src, unsigned char *base, uint64_t *bars,
+                             uint32_t taddr, volatile int *abort_f, volatile int *done_w) {
   using T = PpGeo<UP>;
   constexpr int NG = T::NG, M2 = T::M2, NTH = 32 * PP_CV;
-  const SysDesc &d = in.d;
-  const int total = d.n_sc * d.nsys;
-  const int U = d.U, K = d.K, B = d.B;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int *st_i = reinterpret_cast<const int *>(base + T::INFO);
   const float *sc_i = reinterpret_cast<const float *>(base + T::INFO + 2 * NG * 4);
@@ -288,22 +315,24 @@ __device__ void pp_converter(const InstDesc &in, int ngroups, unsigned char *bas
     }
   };
   for (int g = blockIdx.x; run; g += gridDim.x) {
-    const bool have = g < ngroups;
-    const int rows = have ? pp_group_rows<UP>(d, total, g) : 0;
+    const bool have = g < src.n_groups;
+    const PpGroup G = have ? pp_group<UP>(src, g) : PpGroup{nullptr, 0, 0};
+    const int rows = have ? pp_group_rows<UP>(G) : 0;
     if (have && rows == 0) continue;
 
     // ---- Gram of group g (ordinal o): chunks of 64 antennas ------------------
     if (have) {
+      const int U = G.in->d.U;
       // the thread's items all belong to one system (NTH is a multiple of
       // NG * UP), whose rows it keeps in registers
       const int s_mine = (tid / UP) % NG;
-      const PpSys y_mine = pp_sys(d, total, g * NG + s_mine);
+      const PpSys y_mine = pp_sys(G, s_mine);
       const int nr_mine = y_mine.live ? y_mine.nr : 0;
       const int nch = (rows + PP_GCH - 1) / PP_GCH;
       for (int c = 0; c < nch && run; ++c) {
         const int slot = raw_i % PP_NRAW, st = gop_i & 1;
-        bool w = !*abort_f && mbar_wait(&bars[B_RAWFULL + slot], (raw_i / PP_NRAW) & 1);
-        if (w && gop_i >= 2) w = mbar_wait(&bars[B_GOPEMPTY + st], ((gop_i >> 1) - 1) & 1);
+        bool w = !*abort_f && mbar_wait_ab(&bars[B_RAWFULL + slot], (raw_i / PP_NRAW) & 1, abort_f);
+        if (w && gop_i >= 2) w = mbar_wait_ab(&bars[B_GOPEMPTY + st], ((gop_i >> 1) - 1) & 1, abort_f);
         if (__all_sync(FULL, w)) {
           const unsigned char *rs = base + T::RAW + slot * PP_RAW;
           unsigned char *tile = base + T::GOP + st * PP_TILE;
@@ -311,12 +340,12 @@ __device__ void pp_converter(const InstDesc &in, int ngroups, unsigned char *bas
             const int u = item % UP, s = s_mine, g8 = item / (UP * NG);
             const int left = nr_mine - (c * PP_GCH + 8 * g8);
             const bool live = nr_mine > 0 && u < U;
-            const float2 *src =
+            const float2 *sp =
                 reinterpret_cast<const float2 *>(rs + (size_t)s * PP_GCH * U * 8) + 8 * g8 * U + u;
             float2 v[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-              v[j] = (live && j < left) ? src[j * U] : make_float2(0.f, 0.f);
+              v[j] = (live && j < left) ? sp[j * U] : make_float2(0.f, 0.f);
             uint4 re, im;
             re.x = tc::pack2<BF16>(v[0].x, v[1].x);
             re.y = tc::pack2<BF16>(v[2].x, v[3].x);
@@ -343,8 +372,10 @@ __device__ void pp_converter(const InstDesc &in, int ngroups, unsigned char *bas
 
     // ---- apply of the previous group (ordinal o - 1) -------------------------
     if (prev >= 0) {
+      const PpGroup P = pp_group<UP>(src, prev);
+      const int U = P.in->d.U, K = P.in->d.K, B = P.in->d.B;
       const int po = o - 1, zb = po & 1;
-      bool w = !*abort_f && mbar_wait(&bars[B_ZREADY + zb], (po >> 1) & 1);
+      bool w = !*abort_f && mbar_wait_ab(&bars[B_ZREADY + zb], (po >> 1) & 1, abort_f);
       if (!__all_sync(FULL, w)) {
         *abort_f = 1;
         break;
@@ -352,9 +383,9 @@ __device__ void pp_converter(const InstDesc &in, int ngroups, unsigned char *bas
       PpPend pend{nullptr, 0, 0, 0, 0, 0.f, false};
       bool has_pend = false;
       for (int s = 0; s < NG && run; ++s) {
-        const PpSys y = pp_sys(d, total, prev * NG + s);
+        const PpSys y = pp_sys(P, s);
         if (!y.live) continue;
-        float2 *Xn = in.X + (size_t)y.n * K * B + y.lo;
+        float2 *Xn = P.in->X + (size_t)y.n * K * B + y.lo;
         const bool good = st_i[zb * NG + s] == ST_OK;
         float os = 0.f;
         const uint32_t bb = bsys_i & 1;
@@ -400,7 +431,7 @@ __device__ void pp_converter(const InstDesc &in, int ngroups, unsigned char *bas
         for (int m0 = 0; m0 < y.nr; m0 += PP_MT) {
           const int slot = raw_i % PP_NRAW, at = tile_i & 1;
           const int mrows = min(PP_MT, y.nr - m0);
-          bool wt = !*abort_f && mbar_wait(&bars[B_RAWFULL + slot], (raw_i / PP_NRAW) & 1);
+          bool wt = !*abort_f && mbar_wait_ab(&bars[B_RAWFULL + slot], (raw_i / PP_NRAW) & 1, abort_f);
           if (!__all_sync(FULL, wt)) {
             *abort_f = 1;
             run = false;
@@ -470,12 +501,10 @@ __device__ void pp_converter(const InstDesc &in, int ngroups, unsigned char *bas
 // ----------------------------------------------------------- MMA issuer ---
 // One thread issues the Gram and apply MMAs in the converters' order.
 template <int UP, bool BF16>
-__device__ void pp_issuer(const InstDesc &in, int ngroups, unsigned char *base, uint64_t *bars,
-                          uint32_t taddr, volatile int *abort_f) {
+__device__ void pp_issuer(const PpSrc &src, unsigned char *base, uint64_t *bars, uint32_t taddr,
+                          volatile int *abort_f) {
   using T = PpGeo<UP>;
   constexpr int NG = T::NG;
-  const SysDesc &d = in.d;
-  const int total = d.n_sc * d.nsys;
   const int *st_i = reinterpret_cast<const int *>(base + T::INFO);
   const uint32_t gop_u = smem_u32(base + T::GOP), aop_u = smem_u32(base + T::AOP),
                  bop_u = smem_u32(base + T::BOPS);
@@ -484,17 +513,27 @@ __device__ void pp_issuer(const InstDesc &in, int ngroups, unsigned char *base, 
   uint32_t gop_i = 0, tile_i = 0, bsys_i = 0;
   int o = 0, prev = -1;
   bool ok = true;
+  const int stall_us = src.items ? 0 : src.in0.d.dbg_stall_us;
+  if (stall_us > 0) {
+    // failure injection: wait on a flag that nothing sets, bounded in time;
+    // running out counts as a timed-out wait
+    const volatile int *never = reinterpret_cast<const volatile int *>(base + T::MISC + 8);
+    const uint64_t t0 = globaltimer_ns(), lim = (uint64_t)stall_us * 1000u;
+    while (!*never && globaltimer_ns() - t0 < lim) __nanosleep(256);
+    ok = *never != 0;
+  }
   for (int g = blockIdx.x; ok; g += gridDim.x) {
-    const bool have = g < ngroups;
-    const int rows = have ? pp_group_rows<UP>(d, total, g) : 0;
+    const bool have = g < src.n_groups;
+    const PpGroup G = have ? pp_group<UP>(src, g) : PpGroup{nullptr, 0, 0};
+    const int rows = have ? pp_group_rows<UP>(G) : 0;
     if (have && rows == 0) continue;
     if (have) {
       const int nch = (rows + PP_GCH - 1) / PP_GCH;
       for (int c = 0; c < nch && ok; ++c) {
         const int st = gop_i & 1;
-        ok = !*abort_f && mbar_wait(&bars[B_GOPFULL + st], (gop_i >> 1) & 1);
+        ok = !*abort_f && mbar_wait_ab(&bars[B_GOPFULL + st], (gop_i >> 1) & 1, abort_f);
         // the solvers have read the previous group's Gram out of TMEM
-        if (ok && c == 0 && o >= 1) ok = mbar_wait(&bars[B_GRAMFREE], (o - 1) & 1);
+        if (ok && c == 0 && o >= 1) ok = mbar_wait_ab(&bars[B_GRAMFREE], (o - 1) & 1, abort_f);
         if (!ok) break;
         tc::fence_after_sync();
 #pragma unroll
@@ -508,14 +547,15 @@ __device__ void pp_issuer(const InstDesc &in, int ngroups, unsigned char *base, 
       }
     }
     if (prev >= 0 && ok) {
+      const PpGroup P = pp_group<UP>(src, prev);
       const int zb = (o - 1) & 1;
       for (int s = 0; s < NG && ok; ++s) {
-        const PpSys y = pp_sys(d, total, prev * NG + s);
+        const PpSys y = pp_sys(P, s);
         if (!y.live) continue;
         const uint32_t b0 = bop_u + (bsys_i & 1) * 3 * PP_BOP;
         for (int m0 = 0; m0 < y.nr && ok; m0 += PP_MT) {
           const int at = tile_i & 1;
-          ok = !*abort_f && mbar_wait(&bars[B_AOPFULL + at], (tile_i >> 1) & 1);
+          ok = !*abort_f && mbar_wait_ab(&bars[B_AOPFULL + at], (tile_i >> 1) & 1, abort_f);
           if (!ok) break;
           if (st_i[zb * NG + s] == ST_OK) {  // written before the converters' arrival
             tc::fence_after_sync();
@@ -553,15 +593,11 @@ __device__ void pp_issuer(const InstDesc &in, int ngroups, unsigned char *base, 
 // 2 UP lanes in the split-row form: lane (i, h) holds half h of row i.  The
 // system's symbols are loaded into its z buffer, which the whitening then
 // overwrites with z.
-template <int UP>
-__device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, uint64_t *bars,
-                          uint32_t taddr, volatile int *abort_f) {
+template <int UP, bool BF16>
+__device__ void pp_solver(const PpSrc &src, unsigned char *base, uint64_t *bars, uint32_t taddr,
+                          volatile int *abort_f) {
   using T = PpGeo<UP>;
   constexpr int NG = T::NG, SEG = T::SEG, SPW = T::SPW, HALF = UP / 2;
-  const SysDesc &d = in.d;
-  const int total = d.n_sc * d.nsys;
-  const int U = d.U, K = d.K;
-  const float kappa = d.kappa;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int sw = warp - PP_CV, stid = tid - 32 * PP_CV;  // solver warp, thread
   const int seg = lane / SEG, sl = lane % SEG, i = sl % UP, h = sl / UP;
@@ -570,15 +606,21 @@ __device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, 
   int *st_i = reinterpret_cast<int *>(base + T::INFO);
   float *sc_i = reinterpret_cast<float *>(base + T::INFO + 2 * NG * 4);
   int *ze_i = reinterpret_cast<int *>(base + T::INFO + 4 * NG * 4);
+  int *fix_f = reinterpret_cast<int *>(base + T::MISC + 12);  // the group has a marked system
   int o = 0;
-  for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
-    if (pp_group_rows<UP>(d, total, g) == 0) continue;
-    const int sys = g * NG + sysi, zb = o & 1;
-    const PpSys y = pp_sys(d, total, sys);
+  for (int g = blockIdx.x; g < src.n_groups; g += gridDim.x) {
+    const PpGroup G = pp_group<UP>(src, g);
+    if (pp_group_rows<UP>(G) == 0) continue;
+    const InstDesc &in = *G.in;
+    const SysDesc &d = in.d;
+    const int U = d.U, K = d.K;
+    const float kappa = d.kappa;
+    const int sys = G.sys0 + sysi, zb = o & 1;
+    const PpSys y = pp_sys(G, sysi);
     float2 *Sz = reinterpret_cast<float2 *>(base + T::SZ) + (size_t)(zb * NG + sysi) * PP_KMAX * UP;
     // the converters are done with this buffer's previous group (o - 2)
     bool w = !*abort_f;
-    if (w && o >= 2) w = mbar_wait(&bars[B_ZFREE + zb], ((o >> 1) - 1) & 1);
+    if (w && o >= 2) w = mbar_wait_ab(&bars[B_ZFREE + zb], ((o >> 1) - 1) & 1, abort_f);
     // symbols of this system (zero pads), fetched while the Gram runs
     bool fin_s = true;
     if (w) {
@@ -591,7 +633,7 @@ __device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, 
       }
     }
     // this warp's 32 rows of P (its systems' diagonal blocks)
-    if (w) w = mbar_wait(&bars[B_GRAMDONE], o & 1);
+    if (w) w = mbar_wait_ab(&bars[B_GRAMDONE], o & 1, abort_f);
     w = __all_sync(FULL, w) != 0;
     float v[32];
     if (w) {
@@ -634,9 +676,14 @@ __device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, 
     }
     __syncwarp();
     const bool finite_in = seg_all<SEG>(fin_s && fin_g, lane);
-    float sc = 0.f, zm = 0.f;
+    float sc = 0.f, zm = 0.f, sens = 0.f;
     const int st = split_solve<UP>(row, Gw, Sz, Sz, UP, kappa, d.rho2_sys, d.Es, U, K, sl,
-                                   finite_in, true, sc, zm, d.mrt != 0);
+                                   finite_in, true, sc, zm, d.mrt != 0,
+                                   d.refine == 2 ? &sens : nullptr);
+    // automatic refinement: a flagged system is applied unrefined here and
+    // marked; the fix-up launch of the group kernel redoes its group
+    constexpr float eps = BF16 ? 0x1p-8f : 0x1p-11f;
+    const bool mark = d.refine == 2 && st == ST_OK && eps * sens >= kRefineTrigger;
     int zexp = 0;
     if (zm > 0.f) frexpf(zm, &zexp);
     if (sl == 0) {
@@ -644,12 +691,19 @@ __device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, 
       sc_i[zb * NG + sysi] = sc;
       ze_i[zb * NG + sysi] = zexp;
       if (y.live) {
-        in.status[sys] = st;
+        in.status[sys] = mark ? (int)ST_REFINE : st;
         if (in.scale_out) in.scale_out[sys] = st == ST_OK ? sc : 0.f;
+        if (mark) atomicOr(fix_f, 1);
       }
     }
     if (!bar_and(BAR_SV, 32 * PP_SV, true)) break;
-    if (stid == 0) mbar_arrive(&bars[B_ZREADY + zb]);
+    if (stid == 0) {
+      if (*fix_f) {  // a batch lists the group once for its fix-up launch
+        if (src.fix_list) src.fix_list[atomicAdd(src.fix_count, 1)] = g;
+        *fix_f = 0;
+      }
+      mbar_arrive(&bars[B_ZREADY + zb]);
+    }
     ++o;
   }
 }
@@ -657,7 +711,7 @@ __device__ void pp_solver(const InstDesc &in, int ngroups, unsigned char *base, 
 // --------------------------------------------------------------- kernel ---
 template <int UP, bool BF16>
 __global__ void __launch_bounds__(PP_THREADS, 1)
-    k_pipe_tc(InstDesc in, int ngroups) {
+    k_pipe_tc(PpSrc src) {
   using T = PpGeo<UP>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -676,6 +730,8 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
       mbar_init(&bars[b], per_warp ? PP_CV : 1);
     }
     *abort_f = 0;
+    *reinterpret_cast<volatile int *>(base + T::MISC + 8) = 0;  // the flag nothing sets
+    *reinterpret_cast<volatile int *>(base + T::MISC + 12) = 0;
     for (int w = 0; w < PP_CV; ++w) done_w[w] = 0;
     fence_mbar_init();
   }
@@ -689,29 +745,30 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
   const uint32_t taddr = *tmem_holder;
 
   if (warp < PP_CV) {
-    pp_converter<UP, BF16>(in, ngroups, base, bars, taddr, abort_f, done_w);
+    pp_converter<UP, BF16>(src, base, bars, taddr, abort_f, done_w);
   } else if (warp < PP_CV + PP_SV) {
-    pp_solver<UP>(in, ngroups, base, bars, taddr, abort_f);
+    pp_solver<UP, BF16>(src, base, bars, taddr, abort_f);
   } else if (warp == PP_PRODUCER) {
-    if ((tid & 31) == 0) pp_producer<UP>(in, ngroups, base, bars, abort_f);
+    if ((tid & 31) == 0) pp_producer<UP>(src, base, bars, abort_f);
   } else if ((tid & 31) == 0) {
-    pp_issuer<UP, BF16>(in, ngroups, base, bars, taddr, abort_f);
+    pp_issuer<UP, BF16>(src, base, bars, taddr, abort_f);
   }
   __syncwarp();  // the producer warp's lanes meet again before the CTA barrier
   tc::fence_before_sync();
   __syncthreads();
 
   if (*abort_f) {  // systems of the groups not completed: ST_TIMEOUT, zero rows
-    const SysDesc &d = in.d;
-    const int total = d.n_sc * d.nsys;
     int done = done_w[0];
     for (int w = 1; w < PP_CV; ++w) done = min(done, (int)done_w[w]);
     int o = 0;
-    for (int g = blockIdx.x; g < ngroups; g += gridDim.x) {
-      if (pp_group_rows<UP>(d, total, g) == 0) continue;
+    for (int g = blockIdx.x; g < src.n_groups; g += gridDim.x) {
+      const PpGroup G = pp_group<UP>(src, g);
+      if (pp_group_rows<UP>(G) == 0) continue;
       if (o >= done) {
+        const InstDesc &in = *G.in;
+        const SysDesc &d = in.d;
         for (int s = 0; s < T::NG; ++s) {
-          const PpSys y = pp_sys(d, total, g * T::NG + s);
+          const PpSys y = pp_sys(G, s);
           if (!y.live) continue;
           float2 *Xn = in.X + (size_t)y.n * d.K * d.B + y.lo;
           for (int e = tid; e < y.nr * d.K; e += PP_THREADS) {
@@ -719,8 +776,8 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
             Xn[(size_t)q * d.B + r] = make_float2(0.f, 0.f);
           }
           if (tid == 0) {
-            in.status[g * T::NG + s] = ST_TIMEOUT;
-            if (in.scale_out) in.scale_out[g * T::NG + s] = 0.f;
+            in.status[G.sys0 + s] = ST_TIMEOUT;
+            if (in.scale_out) in.scale_out[G.sys0 + s] = 0.f;
           }
         }
       }
@@ -748,15 +805,46 @@ cudaError_t launch_pipe_t(const SysDesc &d, const float2 *H, const float2 *S, fl
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
   const int grid = ngroups < nsm ? ngroups : nsm;
-  InstDesc in{d, H, S, X, status, scale_out};
-  k_pipe_tc<UP, BF16><<<grid, PP_THREADS, T::BYTES, s>>>(in, ngroups);
+  PpSrc src{InstDesc{d, H, S, X, status, scale_out}, nullptr, nullptr, ngroups, nullptr, nullptr};
+  k_pipe_tc<UP, BF16><<<grid, PP_THREADS, T::BYTES, s>>>(src);
+  return cudaGetLastError();
+}
+
+template <int UP, bool BF16>
+cudaError_t launch_batch_pipe_t(const InstDesc *insts, const WorkItem *items, int n_items,
+                                int *fix_list, int *fix_count, int grid, cudaStream_t s) {
+  using T = PpGeo<UP>;
+  if (n_items == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_pipe_tc<UP, BF16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, T::BYTES);
+  if (e != cudaSuccess) return e;
+  PpSrc src{InstDesc{}, insts, items, n_items, fix_list, fix_count};
+  k_pipe_tc<UP, BF16><<<grid, PP_THREADS, T::BYTES, s>>>(src);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool pipe_tc_supported(const SysDesc &d, int UP) {
-  return (UP == 8 || UP == 16) && d.tma_ok && d.K >= 1 && d.K <= PP_KMAX && !d.refine;
+  return (UP == 8 || UP == 16) && d.tma_ok && d.K >= 1 && d.K <= PP_KMAX && d.refine != 1 &&
+         !d.fixup;
+}
+
+int pipe_systems_per_group(int UP) { return UP == 8 ? PpGeo<8>::NG : PpGeo<16>::NG; }
+
+cudaError_t launch_batch_pipe_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
+                                 int n_items, int *fix_list, int *fix_count, int grid,
+                                 cudaStream_t s) {
+  switch (UP) {
+    case 8:
+      return bf16 ? launch_batch_pipe_t<8, true>(insts, items, n_items, fix_list, fix_count, grid, s)
+                  : launch_batch_pipe_t<8, false>(insts, items, n_items, fix_list, fix_count, grid, s);
+    case 16:
+      return bf16 ? launch_batch_pipe_t<16, true>(insts, items, n_items, fix_list, fix_count, grid, s)
+                  : launch_batch_pipe_t<16, false>(insts, items, n_items, fix_list, fix_count, grid, s);
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_pipe_tc(const SysDesc &d, int UP, bool bf16, const float2 *H,

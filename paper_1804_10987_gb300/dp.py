@@ -84,6 +84,7 @@ def load(build_if_missing: bool = True):
         L.dp_precode.argtypes = [P, P, P, P]
         L.dp_precode_host.argtypes = [P, P, P, P, I]
         L.dp_status_get.argtypes = [P, P]
+        L.dp_debug_stall.argtypes = [P, I]
         L.dp_status_string.argtypes = [I]
         L.dp_status_string.restype = ctypes.c_char_p
         L.dp_version.restype = ctypes.c_char_p
@@ -94,8 +95,10 @@ def load(build_if_missing: bool = True):
         L.dp_batch_status_get.argtypes = [P, P]
         L.dp_batch_describe.argtypes = [P]
         L.dp_batch_describe.restype = ctypes.c_char_p
+        L.dp_batch_set_timing.argtypes = [P, I]
+        L.dp_batch_bucket_ms.argtypes = [P, P, I]
         for name in ("dp_batch_create", "dp_batch_destroy", "dp_batch_precode", "dp_batch_tune",
-                     "dp_batch_status_get"):
+                     "dp_batch_status_get", "dp_batch_set_timing", "dp_batch_bucket_ms"):
             getattr(L, name).restype = I
         U64 = ctypes.c_ulonglong
         L.dp_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(P)]
@@ -117,7 +120,7 @@ def load(build_if_missing: bool = True):
             getattr(L, name).restype = I
         for name in ("dp_plan_create", "dp_plan_destroy", "dp_plan_set_stream", "dp_gram_local",
                      "dp_gram_reduce", "dp_solve", "dp_precode_apply", "dp_precode",
-                     "dp_status_get"):
+                     "dp_status_get", "dp_debug_stall"):
             getattr(L, name).restype = I
         _ = (F,)
         _lib = L
@@ -213,6 +216,11 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+    def debug_stall(self, microseconds: int):
+        """Failure injection for tests: the warp-specialized kernel's bounded
+        wait on a flag that nothing sets (dp_debug_stall); 0 turns it off."""
+        _check(self._lib.dp_debug_stall(self._h, int(microseconds)), "dp_debug_stall")
 
     def set_stream(self, stream):
         self._stream = stream
@@ -356,6 +364,19 @@ class Batch:
     def describe(self) -> dict:
         import json
         return json.loads(self._lib.dp_batch_describe(self._h).decode())
+
+    def set_timing(self, mode: int):
+        """Per-bucket CUDA events: 1 inside the graph, 2 with eager launches,
+        0 off (dp_batch_set_timing)."""
+        _check(self._lib.dp_batch_set_timing(self._h, int(mode)), "dp_batch_set_timing")
+
+    def bucket_ms(self):
+        """Device time of each bucket of the last call (waits for the stream)."""
+        n = len(self.describe()["buckets"])
+        out = np.zeros(max(n, 1), np.float32)
+        _check(self._lib.dp_batch_bucket_ms(self._h, out.ctypes.data_as(ctypes.c_void_p), n),
+               "dp_batch_bucket_ms")
+        return [float(x) for x in out[:n]]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -22,6 +22,16 @@ def rel_err_per_sc(Xg: np.ndarray, Xr: np.ndarray) -> np.ndarray:
     return d / np.where(r > 0, r, 1.0)
 
 
+def entry_err_per_sc(Xg: np.ndarray, Xr: np.ndarray) -> np.ndarray:
+    """Per subcarrier: the largest entry error over the B x K block, relative
+    to the block's largest entry (catches a few bad entries that the
+    Frobenius norm would average away)."""
+    n = Xr.shape[0]
+    d = np.abs(Xg.astype(np.complex128) - Xr).reshape(n, -1).max(axis=1)
+    r = np.abs(Xr).reshape(n, -1).max(axis=1)
+    return d / np.where(r > 0, r, 1.0)
+
+
 def oracle_of(p: synth.Problem, mode=None, tau=None, nthreads=8, **kw):
     mode = mode or p.mode
     return oracle.precode(p.H, p.S, p.cluster_sizes, mode, rho2=p.rho2, N0=p.N0, Es=p.Es,
@@ -29,6 +39,8 @@ def oracle_of(p: synth.Problem, mode=None, tau=None, nthreads=8, **kw):
 
 
 def plan_of(p: synth.Problem, mode=None, tau=None, prec="fp32", refine=0, **kw):
+    """A plan for problem p; refine follows the ABI (0 automatic, 1 always,
+    -1 never)."""
     mode = mode or p.mode
     return dp.Plan(p.U, p.B, p.C, p.n_sc, p.K, mode=mode, prec=prec, rho2=p.rho2, N0=p.N0,
                    Es=p.Es, tau=p.tau if tau is None else tau, refine=refine,

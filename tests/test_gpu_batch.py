@@ -22,12 +22,10 @@ def make_instances(n, seed, nsc_range=(3, 40), big=False):
         C = int(g.choice([c for c in synth.C4_C if B % c == 0]))
         mode = ("wf", "fdwf", "zf")[int(g.integers(0, 3))]
         prec = ("bf16", "fp16", "fp32")[int(g.integers(0, 3))]
-        # ZF has no regularizer: cond(G) grows as B/U shrinks and a 16-bit
-        # Gram stays within the 1e-3 bar only for B >> U; draw ZF in FP32
-        if mode == "zf":
-            prec = "fp32"
-            if B < 2 * U:
-                mode = "wf"
+        # ZF has no regularizer and needs B > U; cond(G) grows as B/U shrinks,
+        # which the automatic refinement of the 16-bit Gram takes care of
+        if mode == "zf" and B < 2 * U:
+            mode = "wf"
         chan = "iid" if g.integers(0, 2) == 0 else "kron"
         n_sc = int(g.integers(nsc_range[0], nsc_range[1] + 1))
         K = int(g.choice([1, 7, 14]))

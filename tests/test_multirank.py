@@ -31,7 +31,7 @@ def _rank(rank, world, port, q):
         t = bench.job_time_ms(10.0 + 5.0 * rank, world, "cpu")
         rate = bench.job_rate(1200, world, t)
         g = torch.Generator()
-        g.manual_seed(bench.rank_seed(synth, rank))
+        g.manual_seed(bench.c4_rank_seed(synth, rank))
         shard = torch.randn(8, generator=g, dtype=torch.float64)
         shards = [torch.zeros(8, dtype=torch.float64) for _ in range(world)]
         dist.all_gather(shards, shard)
