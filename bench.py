@@ -55,6 +55,7 @@ KERNEL_SOURCES = {
     "tc": [_CS + f for f in ("dp_tc_impl.cuh", "dp_quad.cuh", "dp_tc.cuh", "dp_blocks.cuh",
                              "dp_common.cuh")],
     "fdsmall": [_CS + f for f in ("dp_fdsmall.cu", "dp_blocks.cuh", "dp_common.cuh")],
+    "rows": [_CS + f for f in ("dp_rowsolve.cu", "dp_blocks.cuh", "dp_common.cuh")],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 PAPER_CONTEXT = ("PD-WF U=16 B=256 C=8 on 8 V100 (one per cluster), K=7: 0.607 ms per "
@@ -220,6 +221,8 @@ def kernel_kind(kernel):
         return "tc"
     if kernel.startswith(("k_batch_fd_small", "k_fd_small")):
         return "fdsmall"
+    if kernel.startswith("k_solve_rows"):
+        return "rows"
     return "fp32"
 
 
@@ -358,6 +361,9 @@ def measure_c4(args, dp, synth, torch, rank, world, local):
         mean = statistics.mean(per_bucket[k])
         fam, upad = bk["family"], bk["users_padded"]
         kern = (f"k_pipe_tc<{upad},{args.prec}>" if fam.startswith("tc_pipe")
+                else f"k_batch_tc<{upad},{args.prec}> Gram + k_solve_rows<{upad}> + "
+                     f"k_batch_tc<{upad},{args.prec}> apply"
+                if fam.startswith("tc_split")
                 else f"k_batch_tc<{upad},{args.prec}>" if fam.startswith("tc")
                 else f"k_batch_fd_small<{upad}>" if fam == "fd_small_clusters"
                 else f"k_batch_fused<{upad}>")
@@ -379,7 +385,7 @@ def measure_c4(args, dp, synth, torch, rank, world, local):
                                / peak}}
     out = {"value": job_rate(n_sc * args.steps, world, ms_total), "ms_per_step": ms_total / args.steps,
            "subcarriers": n_sc, "roofline": roofline, "buckets": buckets, "clocks": clocks,
-           "gpu_launches": args.steps * len(buckets),
+           "gpu_launches": args.steps * sum(bk.get("launches", 1) for bk in info["buckets"]),
            "streaming_instances": info["streaming_instances"], "shapes": shapes}
     b.close()
     return out, Hs, Ss, Xs

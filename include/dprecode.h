@@ -226,7 +226,8 @@ dp_status dp_status_get(dp_plan_t plan, int *host_status);
  *   NULL allowed) and returns the first failure.
  * dp_batch_describe: a JSON string (owned by the batch) with the buckets,
  *   their work items, systems, algorithmic bytes (every system's H and X
- *   rows and the symbols it reads, once each) and the chosen CTAs per SM.
+ *   rows and the symbols it reads, once each), the chosen CTAs per SM and
+ *   the kernel launches each bucket makes per call.
  * dp_batch_set_timing: mode 1 records a CUDA event before every bucket launch
  *   and one after the last, inside the graph; mode 2 does the same with
  *   eager launches (no graph); 0 turns it off.  Synchronizes the stream and

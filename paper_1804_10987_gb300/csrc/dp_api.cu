@@ -20,6 +20,8 @@ struct dp_plan {
   bool fused_fits = false;
   int *d_off = nullptr;     // [C + 1]
   int *d_status = nullptr;  // [n_sc * nsys]: status of every system of the last call
+  int *d_fix = nullptr;     // reduced precision: groups to redo (list, then its count)
+  int n_fix = 0;            // entries of the list
   int nsys = 1;
   int dbg_stall_us = 0;  // failure injection for tests (dp_debug_stall)
   // FD-WF clusters with B_c < U (<= 32) run the B_c x B_c form
@@ -250,10 +252,17 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
     delete p;
     return DP_ERR_CUDA;
   }
+  if (d.prec != DP_FP32) {
+    const int ng = dp::tc_systems_per_group(p->UP);
+    p->n_fix = (int)((status_len(d) + ng - 1) / ng);
+  }
   if (cudaMalloc(&p->d_off, sizeof(int) * (d.C + 1)) != cudaSuccess ||
-      cudaMalloc(&p->d_status, sizeof(int) * status_len(d)) != cudaSuccess) {
+      cudaMalloc(&p->d_status, sizeof(int) * status_len(d)) != cudaSuccess ||
+      (p->n_fix && cudaMalloc(&p->d_fix, sizeof(int) * (p->n_fix + 1)) != cudaSuccess)) {
     cudaGetLastError();
     cudaFree(p->d_off);
+    cudaFree(p->d_status);
+    cudaFree(p->d_fix);
     delete p;
     return DP_ERR_OOM;
   }
@@ -263,6 +272,7 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
     cudaGetLastError();
     cudaFree(p->d_off);
     cudaFree(p->d_status);
+    cudaFree(p->d_fix);
     delete p;
     return DP_ERR_CUDA;
   }
@@ -277,6 +287,7 @@ dp_status dp_plan_destroy(dp_plan_t p) {
   free_host_pipeline(p);
   cudaFree(p->d_off);
   cudaFree(p->d_status);
+  cudaFree(p->d_fix);
   cudaFree(p->w_G);
   cudaFree(p->w_Z);
   cudaFree(p->w_scale);
@@ -355,15 +366,21 @@ cudaError_t precode_range(dp_plan *p, const float2 *h, const float2 *sy, float2 
     if (e != cudaSuccess || p->all_small) return e;
   }
   if (p->d.prec != DP_FP32 && dp::pipe_tc_supported(sd, p->UP)) {
-    e = dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
-                           p->stream);
-    if (e != cudaSuccess || sd.refine != 2) return e;
-    // automatic refinement: the group kernel redoes the groups whose systems
-    // the warp-specialized kernel marked (its other CTAs exit at once)
-    dp::SysDesc fx = sd;
-    fx.fixup = 1;
-    return dp::launch_fused_tc(fx, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
-                               p->stream);
+    const bool fix = sd.refine == 2 && p->d_fix;
+    int *list = fix ? p->d_fix : nullptr, *count = fix ? p->d_fix + p->n_fix : nullptr;
+    if (fix) e = cudaMemsetAsync(count, 0, sizeof(int), p->stream);
+    if (e == cudaSuccess)
+      e = dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
+                             p->stream, list, count);
+    if (e != cudaSuccess || !fix) return e;
+    // automatic precision escalation: the group kernel redoes the groups the
+    // warp-specialized kernel listed (with an empty list its CTAs leave at once)
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    return dp::launch_fixup_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, list, count,
+                               nsm, p->stream);
   }
   if (p->d.prec != DP_FP32)
     return dp::launch_fused_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,

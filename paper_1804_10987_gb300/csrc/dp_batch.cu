@@ -48,6 +48,10 @@ struct Bucket {
   bool fix = false;
   int *d_fix = nullptr;
   int fix_blocks = 1;
+  // tensor-core family with many users: Gram, solve and apply as three
+  // launches through a workspace (none of its instances refines every system)
+  bool split = false, forced_refine = false;
+  dp::SplitWs ws{};
 };
 
 struct Inst {
@@ -137,7 +141,7 @@ struct dp_batch {
   std::vector<int> streaming;            // instances of the streaming family
   dp::InstDesc *d_insts = nullptr;        // device table, rewritten every call
   std::vector<dp::InstDesc> h_insts;
-  int *d_queues = nullptr;                // one counter per bucket
+  int *d_queues = nullptr;                // three counters per bucket
   int *d_status = nullptr;
   size_t status_len = 0;
   cudaGraph_t graph = nullptr;
@@ -158,6 +162,10 @@ void free_batch(dp_batch *b) {
   for (auto &bk : b->buckets) {
     cudaFree(bk.d_items);
     cudaFree(bk.d_fix);
+    cudaFree(bk.ws.G);
+    cudaFree(bk.ws.Z);
+    cudaFree(bk.ws.sc);
+    cudaFree(bk.ws.st);
   }
   for (auto &in : b->insts) {
     cudaFree(in.w_G);
@@ -176,7 +184,8 @@ void free_batch(dp_batch *b) {
 cudaError_t enqueue_bucket(dp_batch *b, int k, cudaStream_t s) {
   Bucket &bk = b->buckets[k];
   if (bk.items.empty()) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(b->d_queues + k, 0, sizeof(int), s);
+  int *q = b->d_queues + 3 * k;  // three counters per bucket
+  cudaError_t e = cudaMemsetAsync(q, 0, 3 * sizeof(int), s);
   if (e != cudaSuccess) return e;
   const int n = (int)bk.items.size();
   const int grid = std::max(1, std::min<int>(bk.blocks * b->n_sm, n));
@@ -187,18 +196,24 @@ cudaError_t enqueue_bucket(dp_batch *b, int k, cudaStream_t s) {
                                  std::min(b->n_sm, n), s);
     if (e != cudaSuccess || !bk.fix) return e;
     // automatic refinement: the group kernel redoes the listed groups
-    return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, b->d_queues + k,
-                               bk.Kmax, std::max(1, bk.fix_blocks * b->n_sm), s, bk.d_fix,
-                               bk.d_fix + n);
+    return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, q, bk.Kmax,
+                               std::max(1, bk.fix_blocks * b->n_sm), s, bk.d_fix, bk.d_fix + n);
+  }
+  if (bk.family == FAM_TC && bk.split) {
+    for (int ph = 1; ph <= 3 && e == cudaSuccess; ++ph)
+      e = (ph == 2 && dp::row_solve_supported(bk.UP))
+              ? dp::launch_solve_rows(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, q + 1, bk.ws,
+                                      std::min(b->n_sm, n), s)
+              : dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, q + ph - 1,
+                                    bk.Kmax, grid, s, nullptr, nullptr, ph, bk.ws);
+    return e;
   }
   if (bk.family == FAM_TC)
-    return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, (int)bk.items.size(),
-                               b->d_queues + k, bk.Kmax, grid, s);
+    return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, q, bk.Kmax, grid, s);
   if (bk.family == FAM_FDSMALL)
-    return dp::launch_batch_fd_small(bk.UP, b->d_insts, bk.d_items, (int)bk.items.size(),
-                                     b->d_queues + k, bk.Kmax, grid, s);
-  return dp::launch_batch_fused(bk.UP, b->d_insts, bk.d_items, (int)bk.items.size(),
-                                b->d_queues + k, bk.maxrows, bk.Kmax, grid, s);
+    return dp::launch_batch_fd_small(bk.UP, b->d_insts, bk.d_items, n, q, bk.Kmax, grid, s);
+  return dp::launch_batch_fused(bk.UP, b->d_insts, bk.d_items, n, q, bk.maxrows, bk.Kmax, grid,
+                                s);
 }
 
 cudaError_t enqueue_streaming(dp_batch *b, int i, cudaStream_t s) {
@@ -303,13 +318,18 @@ void describe(dp_batch *b) {
     std::snprintf(buf, sizeof buf,
                   "%s{\"family\": \"%s\", \"users_padded\": %d, \"items\": %zu, "
                   "\"systems\": %lld, \"alg_bytes\": %.0f, "
-                  "\"ctas_per_sm\": %d, \"max_ctas_per_sm\": %d, \"tuned_ms\": %.4f}",
+                  "\"ctas_per_sm\": %d, \"max_ctas_per_sm\": %d, \"tuned_ms\": %.4f, "
+                  "\"launches\": %d}",
                   k ? ", " : "",
-                  bk.family == FAM_TC ? (bk.bf16 ? "tc_bf16" : "tc_fp16")
+                  bk.family == FAM_TC ? (bk.split ? (bk.bf16 ? "tc_split_bf16" : "tc_split_fp16")
+                                               : (bk.bf16 ? "tc_bf16" : "tc_fp16"))
                   : bk.family == FAM_PIPE ? (bk.bf16 ? "tc_pipe_bf16" : "tc_pipe_fp16")
                   : bk.family == FAM_FDSMALL ? "fd_small_clusters" : "fp32_fused", bk.UP,
                   bk.items.size(), bk.systems, bk.alg_bytes, bk.blocks, bk.max_blocks,
-                  bk.tuned_ms);
+                  bk.tuned_ms,
+                  bk.items.empty() ? 0
+                  : bk.family == FAM_PIPE ? (bk.fix ? 2 : 1)
+                  : (bk.family == FAM_TC && bk.split) ? 3 : 1);
     s += buf;
   }
   char tail[64];
@@ -461,6 +481,7 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
     bk.Kmax = std::max(bk.Kmax, in.d.K);
     bk.maxrows = std::max(bk.maxrows, in.maxrows);
     if (in.family == FAM_PIPE && sys_of(in, nullptr).refine == 2) bk.fix = true;
+    if (sys_of(in, nullptr).refine == 1) bk.forced_refine = true;
     const int per = in.family == FAM_TC   ? dp::tc_systems_per_group(in.UP)
                     : in.family == FAM_PIPE ? dp::pipe_systems_per_group(in.UP)
                                             : 1;
@@ -507,6 +528,20 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
                         : bk.family == FAM_FDSMALL
                               ? dp::fd_small_max_blocks_per_sm(bk.UP, bk.Kmax)
                               : dp::fused_max_blocks_per_sm(bk.UP, bk.maxrows, bk.Kmax);
+    if (bk.family == FAM_TC && bk.UP > 32 && !bk.forced_refine) {
+      const size_t ni = bk.items.size(), ng = (size_t)dp::tc_systems_per_group(bk.UP);
+      bk.split = true;
+      bk.ws.kmax = bk.Kmax;
+      if (cudaMalloc(&bk.ws.G, sizeof(float2) * ni * ng * bk.UP * bk.UP) != cudaSuccess ||
+          cudaMalloc(&bk.ws.Z, sizeof(float2) * ni * ng * std::max(1, bk.Kmax) * bk.UP) !=
+              cudaSuccess ||
+          cudaMalloc(&bk.ws.sc, sizeof(float) * ni * ng) != cudaSuccess ||
+          cudaMalloc(&bk.ws.st, sizeof(int) * ni * ng) != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return DP_ERR_OOM;
+      }
+    }
     if (bk.fix) {
       bk.fix_blocks = dp::tc_max_blocks_per_sm(bk.UP, bk.bf16, bk.Kmax);
       if (bk.fix_blocks < 1 ||
@@ -522,7 +557,8 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
     }
     bk.blocks = bk.max_blocks;
   }
-  if (cudaMalloc(&b->d_queues, sizeof(int) * std::max<size_t>(1, b->buckets.size())) != cudaSuccess) {
+  if (cudaMalloc(&b->d_queues, 3 * sizeof(int) * std::max<size_t>(1, b->buckets.size())) !=
+      cudaSuccess) {
     free_batch(b);
     return DP_ERR_OOM;
   }

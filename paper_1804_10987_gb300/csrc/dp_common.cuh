@@ -173,8 +173,6 @@ struct SysDesc {
   int refine;       // tensor-core path, one step of iterative refinement of z:
                     // 0 never, 1 every system, 2 systems the trigger flags
   int mrt;          // maximum ratio transmission: no inverse, z = s, t = tr(G)
-  int fixup;        // k_fused_tc: only groups holding ST_REFINE systems (the
-                    // automatic refinement after the warp-specialized kernel)
   int dbg_stall_us; // failure injection (tests): the warp-specialized kernel's
                     // MMA issuer first waits this long on a flag that nothing
                     // sets, then gives up as a timed-out wait does; 0: off
@@ -189,6 +187,17 @@ struct InstDesc {
   float2 *X;
   int *status;
   float *scale_out;
+};
+
+// Workspace of the split tensor-core form (Gram, solve and apply as three
+// launches over one bucket's work items), per work item and system:
+// G [UP][UP], z [kmax][UP], scale, status.
+struct SplitWs {
+  float2 *G;
+  float2 *Z;
+  float *sc;
+  int *st;
+  int kmax;
 };
 
 // A unit of work of a persistent kernel: systems [sys0, sys0 + nact) of

@@ -59,8 +59,11 @@ struct TcOps {
                            float2 *X, int *status, float *scale_out, cudaStream_t s);
   static cudaError_t batch(bool bf16, const InstDesc *insts, const WorkItem *items, int n_items,
                            int *queue, int Kmax, int grid, cudaStream_t s, const int *fix_list,
-                           const int *fix_count);
+                           const int *fix_count, int phase, const SplitWs &ws);
   static int blocks(bool bf16, int Kmax);
+  static cudaError_t fixup(const SysDesc &d, bool bf16, const float2 *H, const float2 *S,
+                           float2 *X, int *status, const int *fix_list, const int *fix_count,
+                           int grid, cudaStream_t s);
 };
 
 cudaError_t launch_gram(const SysDesc &d, int UP, const float2 *H, float2 *Gout,
@@ -88,15 +91,27 @@ int tc_systems_per_group(int UP);
 // With fix_count non-NULL it takes only items[fix_list[i]], i < *fix_count
 // (the fix-up after the warp-specialized kernel; its CTAs exit at once when
 // the count is 0).
+// phase: 0 every step in one launch; 1 Gram, 2 solve, 3 apply of the split
+// form, through the workspace ws (sized for n_items work items).
 cudaError_t launch_batch_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
                             int n_items, int *queue, int Kmax, int grid, cudaStream_t s,
-                            const int *fix_list = nullptr, const int *fix_count = nullptr);
+                            const int *fix_list = nullptr, const int *fix_count = nullptr,
+                            int phase = 0, const SplitWs &ws = SplitWs{});
 int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax);
 // Warp-specialized persistent form of the same arithmetic (bit-identical),
 // for users padded to 8 or 16, 1 <= K <= 16 and bulk-copyable rows.
 bool pipe_tc_supported(const SysDesc &d, int UP);
+// fix_list / fix_count (may be NULL): with automatic refinement the groups
+// (of tc_systems_per_group(UP) systems) holding flagged systems are appended
+// there (the count zeroed before the launch), for launch_fixup_tc.
 cudaError_t launch_pipe_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
-                           float2 *X, int *status, float *scale_out, cudaStream_t s);
+                           float2 *X, int *status, float *scale_out, cudaStream_t s,
+                           int *fix_list = nullptr, int *fix_count = nullptr);
+// The group kernel over those listed groups (grid CTAs; nothing when the
+// list is empty).
+cudaError_t launch_fixup_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
+                            float2 *X, int *status, const int *fix_list, const int *fix_count,
+                            int grid, cudaStream_t s);
 // The same kernel over a batch bucket's work items (groups of up to
 // pipe_systems_per_group(UP) systems of one instance), one CTA per SM (grid);
 // with automatic refinement the groups holding marked systems are appended
@@ -105,6 +120,14 @@ int pipe_systems_per_group(int UP);
 cudaError_t launch_batch_pipe_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
                                  int n_items, int *fix_list, int *fix_count, int grid,
                                  cudaStream_t s);
+
+// The split form's solve phase for 40..64 padded users with one row of A per
+// thread (four systems per CTA, one CTA per SM: grid = SMs); same workspace
+// and queue conventions as launch_batch_tc's phase 2.
+bool row_solve_supported(int UP);
+cudaError_t launch_solve_rows(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
+                              int n_items, int *queue, const SplitWs &ws, int grid,
+                              cudaStream_t s);
 
 // FD-WF clusters with B_c < U (and B_c <= 32) in the B_c x B_c form:
 // padded cluster width (8, 16, 32; 0 if none fits) and the launchers.

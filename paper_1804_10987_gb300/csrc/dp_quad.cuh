@@ -130,22 +130,24 @@ __device__ void quad_solve(const float2 *Gs, const float2 *Ss, float2 *Zs, int *
           bad = bad || !(piv > 0.f) || !isfinite(piv);
           const float ip = 1.f / piv;
           const float2 fv = cscale(f, ip);
-          float2 rv[QW];
-#pragma unroll
-          for (int c = 0; c < QW; c += 2) {
-            const float4 w = *reinterpret_cast<const float4 *>(rp + q * QS + c);
-            rv[c] = make_float2(w.x, w.y);
-            rv[c + 1] = make_float2(w.z, w.w);
-          }
+          const float4 *rq = reinterpret_cast<const float4 *>(rp + q * QS);
+          // row p two entries at a time, used as read (few live registers)
           if (i == p) {
 #pragma unroll
-            for (int c = 0; c < QW; ++c)
-              a[c] = (c == pr && q == qp) ? make_float2(ip, 0.f) : cscale(rv[c], ip);
+            for (int c = 0; c < QW; c += 2) {
+              const float4 w = rq[c / 2];
+              a[c] = (c == pr && q == qp) ? make_float2(ip, 0.f) : make_float2(w.x * ip, w.y * ip);
+              a[c + 1] = (c + 1 == pr && q == qp) ? make_float2(ip, 0.f)
+                                                  : make_float2(w.z * ip, w.w * ip);
+            }
           } else {
 #pragma unroll
-            for (int c = 0; c < QW; ++c) {
+            for (int c = 0; c < QW; c += 2) {
+              const float4 w = rq[c / 2];
               if (c == pr && q == qp) a[c] = make_float2(-fv.x, -fv.y);
-              else cmsub(a[c], fv, rv[c]);
+              else cmsub(a[c], fv, make_float2(w.x, w.y));
+              if (c + 1 == pr && q == qp) a[c + 1] = make_float2(-fv.x, -fv.y);
+              else cmsub(a[c + 1], fv, make_float2(w.z, w.w));
             }
           }
           if (i == p + 1) {  // publish the next pivot row

@@ -35,9 +35,10 @@ int tc_systems_per_group(int UP) {
 
 cudaError_t launch_batch_tc(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
                             int n_items, int *queue, int Kmax, int grid, cudaStream_t s,
-                            const int *fix_list, const int *fix_count) {
+                            const int *fix_list, const int *fix_count, int phase,
+                            const SplitWs &ws) {
   DP_TC_DISPATCH(UP, O::batch(bf16, insts, items, n_items, queue, Kmax, grid, s, fix_list,
-                              fix_count),
+                              fix_count, phase, ws),
                  cudaErrorInvalidValue);
 }
 
@@ -48,6 +49,13 @@ int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax) {
 cudaError_t launch_fused_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
                             float2 *X, int *status, float *scale_out, cudaStream_t s) {
   DP_TC_DISPATCH(UP, O::fused(d, bf16, H, S, X, status, scale_out, s), cudaErrorInvalidValue);
+}
+
+cudaError_t launch_fixup_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
+                            float2 *X, int *status, const int *fix_list, const int *fix_count,
+                            int grid, cudaStream_t s) {
+  DP_TC_DISPATCH(UP, O::fixup(d, bf16, H, S, X, status, fix_list, fix_count, grid, s),
+                 cudaErrorInvalidValue);
 }
 
 }  // namespace dp

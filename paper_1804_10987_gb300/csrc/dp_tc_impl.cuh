@@ -318,8 +318,16 @@ __device__ bool tc_apply(TcCtx &cx, const SysDesc &d, const float2 *__restrict__
 // Systems [sys0, sys0 + nact) of one instance (nact <= NG): Gram on the tensor
 // cores, solve, apply.  Returns false if a bounded wait gave up (the
 // systems' outputs are then zeroed and their status set to ST_TIMEOUT).
-template <int UP, bool BF16>
-__device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
+// Phases of tc_group: PH_FUSED runs every step; the split form runs the
+// Gram (PH_GRAM: G and its finiteness to the workspace), the solve (PH_SOLVE:
+// G from the workspace; z, scale and status back to it) and the apply
+// (PH_APPLY) as three launches over the same work items, so that the solve
+// -- ALU-bound for many users -- does not hold the streaming phases.
+enum : int { PH_FUSED = 0, PH_GRAM = 1, PH_SOLVE = 2, PH_APPLY = 3 };
+
+template <int UP, bool BF16, int PH = PH_FUSED>
+__device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
+                         const SplitWs *ws = nullptr, int it = 0) {
   using T = TcGeo<UP>;
   constexpr int NG = T::NG, M2 = T::M2;
   const SysDesc &d = in.d;
@@ -382,18 +390,35 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   int kmax = 0;
   for (int s = 0; s < NG; ++s) kmax = max(kmax, nr_s[s]);
   const int nchunks = (kmax + KC - 1) / KC;
-  for (int e = tid; e < NG * K * UP; e += NT) {
-    const int s = e / (K * UP), r = e - s * K * UP, k = r / UP, u = r - k * UP;
-    float2 v = make_float2(0.f, 0.f);
-    if (s < nact && u < U) v = __ldg(S + ((size_t)n_s[s] * K + k) * U + u);
-    Ss[e] = v;
+  if constexpr (PH == PH_FUSED || PH == PH_SOLVE) {
+    for (int e = tid; e < NG * K * UP; e += NT) {
+      const int s = e / (K * UP), r = e - s * K * UP, k = r / UP, u = r - k * UP;
+      float2 v = make_float2(0.f, 0.f);
+      if (s < nact && u < U) v = __ldg(S + ((size_t)n_s[s] * K + k) * U + u);
+      Ss[e] = v;
+    }
   }
+  if constexpr (PH == PH_APPLY) {
+    // z, scale and status of the group's systems from the workspace
+    for (int e = tid; e < NG * K * UP; e += NT) {
+      const int s = e / (K * UP), r = e - s * K * UP;
+      Zs[e] = ws->Z[((size_t)it * NG + s) * ws->kmax * UP + r];
+    }
+    if (tid < NG) {
+      sc_s[tid] = ws->sc[it * NG + tid];
+      st_s[tid] = ws->st[it * NG + tid];
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    return tc_apply<UP>(cx, d, H, X, nact, true);
+  }
+  bool ok = true;
+  if constexpr (PH == PH_FUSED || PH == PH_GRAM) {
 
   // ---- Gram mainloop --------------------------------------------------------
   const uint32_t idesc = tc::idesc_f16(128, 128, BF16);
   const uint32_t tiles_u32 = smem_u32(tiles);
   uint64_t *bar_mma = bar_tma + 1;
-  bool ok = true;
   for (int c = 0; c < nchunks && ok; ++c) {
     const int buf = c & 1;
     // the MMAs of chunk c - 2 read this tile
@@ -448,6 +473,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
       if (tid == 0) {
         status[sys0 + s] = ST_TIMEOUT;
         if (scale_out) scale_out[sys0 + s] = 0.f;
+        if constexpr (PH == PH_GRAM) ws->st[it * NG + s] = ST_TIMEOUT;  // the later phases keep it
       }
     }
     return false;
@@ -533,16 +559,32 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
       Gs[e] = g;
     }
   }
+  }  // PH_FUSED, PH_GRAM
+  if constexpr (PH == PH_SOLVE) {  // G and its finiteness from the workspace
+    for (int e = tid; e < NG * UP * UP; e += NT) Gs[e] = ws->G[(size_t)it * NG * UP * UP + e];
+    if (tid < NG) st_s[tid] = ws->st[it * NG + tid];
+  }
   __syncthreads();
   // per-system finiteness of G (covers H) and of the symbols
   if (warp < NG) {
     bool fin = true;
-    for (int e = lane; e < UP * UP; e += 32) fin = fin && cfinite(Gs[warp * UP * UP + e]);
-    for (int e = lane; e < K * UP; e += 32) fin = fin && cfinite(Ss[warp * K * UP + e]);
+    if constexpr (PH != PH_SOLVE)
+      for (int e = lane; e < UP * UP; e += 32) fin = fin && cfinite(Gs[warp * UP * UP + e]);
+    if constexpr (PH != PH_GRAM)
+      for (int e = lane; e < K * UP; e += 32) fin = fin && cfinite(Ss[warp * K * UP + e]);
     fin = __all_sync(FULL, fin);
-    if (lane == 0) st_s[warp] = fin ? ST_OK : ST_NONFINITE;
+    if constexpr (PH == PH_SOLVE) {  // the Gram phase's verdict stands
+      if (lane == 0 && st_s[warp] == ST_OK && !fin) st_s[warp] = ST_NONFINITE;
+    } else {
+      if (lane == 0) st_s[warp] = fin ? ST_OK : ST_NONFINITE;
+    }
   }
   __syncthreads();
+  if constexpr (PH == PH_GRAM) {  // G and its finiteness to the workspace
+    for (int e = tid; e < NG * UP * UP; e += NT) ws->G[(size_t)it * NG * UP * UP + e] = Gs[e];
+    if (tid < NG) ws->st[it * NG + tid] = st_s[tid];
+    return true;
+  }
 
   const bool refine = d.refine && !d.mrt;
   if constexpr (UP >= 24) {
@@ -589,7 +631,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
   const bool any_rf = __syncthreads_or(tid < NG && rf_s[tid]) != 0;
   const bool any_es = __syncthreads_or(tid < NG && es_s[tid]) != 0;
 
-  ok = tc_apply<UP>(cx, d, H, X, nact, ok, any_es ? nes_s : nullptr);
+  if constexpr (PH == PH_FUSED) ok = tc_apply<UP>(cx, d, H, X, nact, ok, any_es ? nes_s : nullptr);
 
   if (any_es && ok) {
     // ---- escalation: FP32 Gram (SIMT, register-tiled as the FP32 path's),
@@ -633,10 +675,26 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact) {
     }
     fence_proxy_async_smem();
     __syncthreads();
-    ok = tc_apply<UP>(cx, d, H, X, nact, ok, es_s);
+    if constexpr (PH == PH_FUSED) ok = tc_apply<UP>(cx, d, H, X, nact, ok, es_s);
+  }
+  if constexpr (PH == PH_SOLVE) {  // z, scale and status to the workspace
+    __syncthreads();
+    for (int e = tid; e < NG * K * UP; e += NT) {
+      const int s = e / (K * UP), r = e - s * K * UP;
+      ws->Z[((size_t)it * NG + s) * ws->kmax * UP + r] = Zs[e];
+    }
+    if (tid < NG) {
+      ws->sc[it * NG + tid] = sc_s[tid];
+      ws->st[it * NG + tid] = (tid < nact && !sk_s[tid]) ? st_s[tid] : ST_OK;
+    }
+    if (tid < nact && !sk_s[tid]) {
+      status[sys0 + tid] = st_s[tid];
+      if (scale_out) scale_out[sys0 + tid] = st_s[tid] == ST_OK ? sc_s[tid] : 0.f;
+    }
+    return true;
   }
 
-  for (int step = 1; any_rf && ok && step <= 3; ++step) {
+  for (int step = 1; PH == PH_FUSED && any_rf && ok && step <= 3; ++step) {
     if (tid < NG) act_s[tid] = (tid < nact && rf_s[tid] >= step) ? 1 : 0;
     if (!__syncthreads_or(tid < NG && act_s[tid])) break;
     // ---- a step of iterative refinement of z ---------------------------------
@@ -730,23 +788,40 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
   const int total = in.d.n_sc * in.d.nsys;
   const int sys0 = blockIdx.x * TcGeo<UP>::NG;
   const int nact = min(TcGeo<UP>::NG, total - sys0);
-  if (in.d.fixup) {  // only groups the warp-specialized kernel marked
-    const bool mine = threadIdx.x < nact && in.status[sys0 + threadIdx.x] == ST_REFINE;
-    if (!__syncthreads_or(mine)) return;
-  }
   TcCtx cx;
   tc_setup<UP>(cx, smem_raw, Kmax);
   tc_group<UP, BF16>(cx, in, sys0, nact);
   tc_teardown(cx);
 }
 
+// Fix-up after the warp-specialized kernel (automatic precision escalation):
+// the groups it listed (fix_list[0 .. *fix_count), group g = systems
+// [g NG, g NG + NG)), redone by the group kernel; with an empty list every CTA
+// leaves at once.
+template <int UP, bool BF16>
+__global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
+    k_fixup_tc(InstDesc in, const int *__restrict__ fix_list, const int *__restrict__ fix_count,
+               int Kmax) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = *fix_count;
+  if ((int)blockIdx.x >= n) return;
+  const int total = in.d.n_sc * in.d.nsys;
+  TcCtx cx;
+  tc_setup<UP>(cx, smem_raw, Kmax);
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int sys0 = fix_list[it] * TcGeo<UP>::NG;
+    if (!tc_group<UP, BF16>(cx, in, sys0, min(TcGeo<UP>::NG, total - sys0))) break;
+  }
+  tc_teardown(cx);
+}
+
 // Persistent form: CTAs pull work items (groups of systems of any instance of
 // this bucket) from an atomic queue until it is empty.
-template <int UP, bool BF16>
+template <int UP, bool BF16, int PH = PH_FUSED>
 __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
     k_batch_tc(const InstDesc *__restrict__ insts, const WorkItem *__restrict__ items,
                int n_items, int *__restrict__ queue, int Kmax, const int *__restrict__ fix_list,
-               const int *__restrict__ fix_count) {
+               const int *__restrict__ fix_count, SplitWs ws) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ int next;
   // fix-up form (automatic refinement after the warp-specialized kernel):
@@ -760,8 +835,9 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
     __syncthreads();
     const int it = next;
     if (it >= n) break;
-    const WorkItem w = items[fix_list ? fix_list[it] : it];
-    if (!tc_group<UP, BF16>(cx, insts[w.inst], w.sys0, w.nact)) break;
+    const int item = fix_list ? fix_list[it] : it;
+    const WorkItem w = items[item];
+    if (!tc_group<UP, BF16, PH>(cx, insts[w.inst], w.sys0, w.nact, &ws, item)) break;
   }
   tc_teardown(cx);
 }
@@ -783,20 +859,42 @@ cudaError_t launch_tc_t(const SysDesc &d, const float2 *H, const float2 *S, floa
   return cudaGetLastError();
 }
 
+template <int UP, bool BF16, int PH>
+cudaError_t launch_batch_tc_ph(const InstDesc *insts, const WorkItem *items, int n_items,
+                               int *queue, int Kmax, int grid, cudaStream_t s,
+                               const int *fix_list, const int *fix_count, const SplitWs &ws) {
+  const TcSmem L = tc_smem_layout<UP>(Kmax);
+  cudaError_t e = cudaFuncSetAttribute(k_batch_tc<UP, BF16, PH>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_batch_tc<UP, BF16, PH>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  k_batch_tc<UP, BF16, PH><<<grid, NT, L.total, s>>>(insts, items, n_items, queue, Kmax,
+                                                      fix_list, fix_count, ws);
+  return cudaGetLastError();
+}
+
 template <int UP, bool BF16>
 cudaError_t launch_batch_tc_t(const InstDesc *insts, const WorkItem *items, int n_items,
                               int *queue, int Kmax, int grid, cudaStream_t s,
-                              const int *fix_list, const int *fix_count) {
-  const TcSmem L = tc_smem_layout<UP>(Kmax);
-  cudaError_t e = cudaFuncSetAttribute(k_batch_tc<UP, BF16>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_batch_tc<UP, BF16>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
-  k_batch_tc<UP, BF16><<<grid, NT, L.total, s>>>(insts, items, n_items, queue, Kmax, fix_list,
-                                                  fix_count);
-  return cudaGetLastError();
+                              const int *fix_list, const int *fix_count, int phase,
+                              const SplitWs &ws) {
+  switch (phase) {
+    case PH_GRAM:
+      return launch_batch_tc_ph<UP, BF16, PH_GRAM>(insts, items, n_items, queue, Kmax, grid, s,
+                                                   fix_list, fix_count, ws);
+    case PH_SOLVE:
+      return launch_batch_tc_ph<UP, BF16, PH_SOLVE>(insts, items, n_items, queue, Kmax, grid, s,
+                                                    fix_list, fix_count, ws);
+    case PH_APPLY:
+      return launch_batch_tc_ph<UP, BF16, PH_APPLY>(insts, items, n_items, queue, Kmax, grid, s,
+                                                    fix_list, fix_count, ws);
+    default:
+      return launch_batch_tc_ph<UP, BF16, PH_FUSED>(insts, items, n_items, queue, Kmax, grid, s,
+                                                    fix_list, fix_count, ws);
+  }
 }
 
 template <int UP>
@@ -804,6 +902,22 @@ cudaError_t launch_tc_u(const SysDesc &d, bool bf16, const float2 *H, const floa
                         int *status, float *scale_out, cudaStream_t s) {
   return bf16 ? launch_tc_t<UP, true>(d, H, S, X, status, scale_out, s)
               : launch_tc_t<UP, false>(d, H, S, X, status, scale_out, s);
+}
+
+template <int UP, bool BF16>
+cudaError_t launch_fixup_tc_t(const SysDesc &d, const float2 *H, const float2 *S, float2 *X,
+                              int *status, const int *fix_list, const int *fix_count, int grid,
+                              cudaStream_t s) {
+  const TcSmem L = tc_smem_layout<UP>(d.K);
+  cudaError_t e = cudaFuncSetAttribute(k_fixup_tc<UP, BF16>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fixup_tc<UP, BF16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  InstDesc in{d, H, S, X, status, nullptr};
+  k_fixup_tc<UP, BF16><<<grid, NT, L.total, s>>>(in, fix_list, fix_count, d.K);
+  return cudaGetLastError();
 }
 
 template <int UP>
@@ -839,11 +953,19 @@ cudaError_t TcOps<UP>::fused(const SysDesc &d, bool bf16, const float2 *H, const
 template <int UP>
 cudaError_t TcOps<UP>::batch(bool bf16, const InstDesc *insts, const WorkItem *items,
                              int n_items, int *queue, int Kmax, int grid, cudaStream_t s,
-                             const int *fix_list, const int *fix_count) {
+                             const int *fix_list, const int *fix_count, int phase,
+                             const SplitWs &ws) {
   return bf16 ? launch_batch_tc_t<UP, true>(insts, items, n_items, queue, Kmax, grid, s, fix_list,
-                                            fix_count)
+                                            fix_count, phase, ws)
               : launch_batch_tc_t<UP, false>(insts, items, n_items, queue, Kmax, grid, s,
-                                             fix_list, fix_count);
+                                             fix_list, fix_count, phase, ws);
+}
+template <int UP>
+cudaError_t TcOps<UP>::fixup(const SysDesc &d, bool bf16, const float2 *H, const float2 *S,
+                             float2 *X, int *status, const int *fix_list, const int *fix_count,
+                             int grid, cudaStream_t s) {
+  return bf16 ? launch_fixup_tc_t<UP, true>(d, H, S, X, status, fix_list, fix_count, grid, s)
+              : launch_fixup_tc_t<UP, false>(d, H, S, X, status, fix_list, fix_count, grid, s);
 }
 template <int UP>
 int TcOps<UP>::blocks(bool bf16, int Kmax) {

@@ -129,9 +129,9 @@ struct PpGroup {
   const InstDesc *in;
   int sys0, nact;
 };
-template <int UP>
+template <int UP, bool BAT>
 __device__ __forceinline__ PpGroup pp_group(const PpSrc &src, int g) {
-  if (src.items) {
+  if constexpr (BAT) {
     const WorkItem w = src.items[g];
     return PpGroup{src.insts + w.inst, w.sys0, w.nact};
   }
@@ -174,7 +174,7 @@ __device__ int pp_group_rows(const PpGroup &G) {
 }
 
 // ------------------------------------------------------------- producer ---
-template <int UP>
+template <int UP, bool BAT>
 __device__ void pp_producer(const PpSrc &src, unsigned char *base, uint64_t *bars,
                             volatile int *abort_f) {
   using T = PpGeo<UP>;
@@ -191,7 +191,7 @@ __device__ void pp_producer(const PpSrc &src, unsigned char *base, uint64_t *bar
   int prev = -1;
   for (int g = blockIdx.x; ok; g += gridDim.x) {
     const bool have = g < src.n_groups;
-    const PpGroup G = have ? pp_group<UP>(src, g) : PpGroup{nullptr, 0, 0};
+    const PpGroup G = have ? pp_group<UP, BAT>(src, g) : PpGroup{nullptr, 0, 0};
     const int rows = have ? pp_group_rows<UP>(G) : 0;
     if (have && rows == 0) continue;
     if (have) {
@@ -219,7 +219,7 @@ __device__ void pp_producer(const PpSrc &src, unsigned char *base, uint64_t *bar
       }
     }
     if (prev >= 0 && ok) {
-      const PpGroup P = pp_group<UP>(src, prev);
+      const PpGroup P = pp_group<UP, BAT>(src, prev);
       const SysDesc &d = P.in->d;
       const size_t rowb = (size_t)d.U * 8;
       for (int s = 0; s < T::NG && ok; ++s) {
@@ -290,7 +290,7 @@ __device__ bool pp_readout(const PpPend &p, int K, int B, uint32_t taddr, uint64
   return true;
 }
 
-template <int UP, bool BF16>
+template <int UP, bool BF16, bool BAT>
 __device__ void pp_converter(const PpSrc &src, unsigned char *base, uint64_t *bars,
                              uint32_t taddr, volatile int *abort_f, volatile int *done_w) {
   using T = PpGeo<UP>;
@@ -316,7 +316,7 @@ __device__ void pp_converter(const PpSrc &src, unsigned char *base, uint64_t *ba
   };
   for (int g = blockIdx.x; run; g += gridDim.x) {
     const bool have = g < src.n_groups;
-    const PpGroup G = have ? pp_group<UP>(src, g) : PpGroup{nullptr, 0, 0};
+    const PpGroup G = have ? pp_group<UP, BAT>(src, g) : PpGroup{nullptr, 0, 0};
     const int rows = have ? pp_group_rows<UP>(G) : 0;
     if (have && rows == 0) continue;
 
@@ -372,7 +372,7 @@ __device__ void pp_converter(const PpSrc &src, unsigned char *base, uint64_t *ba
 
     // ---- apply of the previous group (ordinal o - 1) -------------------------
     if (prev >= 0) {
-      const PpGroup P = pp_group<UP>(src, prev);
+      const PpGroup P = pp_group<UP, BAT>(src, prev);
       const int U = P.in->d.U, K = P.in->d.K, B = P.in->d.B;
       const int po = o - 1, zb = po & 1;
       bool w = !*abort_f && mbar_wait_ab(&bars[B_ZREADY + zb], (po >> 1) & 1, abort_f);
@@ -500,7 +500,7 @@ __device__ void pp_converter(const PpSrc &src, unsigned char *base, uint64_t *ba
 
 // ----------------------------------------------------------- MMA issuer ---
 // One thread issues the Gram and apply MMAs in the converters' order.
-template <int UP, bool BF16>
+template <int UP, bool BF16, bool BAT>
 __device__ void pp_issuer(const PpSrc &src, unsigned char *base, uint64_t *bars, uint32_t taddr,
                           volatile int *abort_f) {
   using T = PpGeo<UP>;
@@ -513,7 +513,7 @@ __device__ void pp_issuer(const PpSrc &src, unsigned char *base, uint64_t *bars,
   uint32_t gop_i = 0, tile_i = 0, bsys_i = 0;
   int o = 0, prev = -1;
   bool ok = true;
-  const int stall_us = src.items ? 0 : src.in0.d.dbg_stall_us;
+  const int stall_us = BAT ? 0 : src.in0.d.dbg_stall_us;
   if (stall_us > 0) {
     // failure injection: wait on a flag that nothing sets, bounded in time;
     // running out counts as a timed-out wait
@@ -524,7 +524,7 @@ __device__ void pp_issuer(const PpSrc &src, unsigned char *base, uint64_t *bars,
   }
   for (int g = blockIdx.x; ok; g += gridDim.x) {
     const bool have = g < src.n_groups;
-    const PpGroup G = have ? pp_group<UP>(src, g) : PpGroup{nullptr, 0, 0};
+    const PpGroup G = have ? pp_group<UP, BAT>(src, g) : PpGroup{nullptr, 0, 0};
     const int rows = have ? pp_group_rows<UP>(G) : 0;
     if (have && rows == 0) continue;
     if (have) {
@@ -547,7 +547,7 @@ __device__ void pp_issuer(const PpSrc &src, unsigned char *base, uint64_t *bars,
       }
     }
     if (prev >= 0 && ok) {
-      const PpGroup P = pp_group<UP>(src, prev);
+      const PpGroup P = pp_group<UP, BAT>(src, prev);
       const int zb = (o - 1) & 1;
       for (int s = 0; s < NG && ok; ++s) {
         const PpSys y = pp_sys(P, s);
@@ -593,7 +593,7 @@ __device__ void pp_issuer(const PpSrc &src, unsigned char *base, uint64_t *bars,
 // 2 UP lanes in the split-row form: lane (i, h) holds half h of row i.  The
 // system's symbols are loaded into its z buffer, which the whitening then
 // overwrites with z.
-template <int UP, bool BF16>
+template <int UP, bool BF16, bool BAT>
 __device__ void pp_solver(const PpSrc &src, unsigned char *base, uint64_t *bars, uint32_t taddr,
                           volatile int *abort_f) {
   using T = PpGeo<UP>;
@@ -609,7 +609,7 @@ __device__ void pp_solver(const PpSrc &src, unsigned char *base, uint64_t *bars,
   int *fix_f = reinterpret_cast<int *>(base + T::MISC + 12);  // the group has a marked system
   int o = 0;
   for (int g = blockIdx.x; g < src.n_groups; g += gridDim.x) {
-    const PpGroup G = pp_group<UP>(src, g);
+    const PpGroup G = pp_group<UP, BAT>(src, g);
     if (pp_group_rows<UP>(G) == 0) continue;
     const InstDesc &in = *G.in;
     const SysDesc &d = in.d;
@@ -709,7 +709,7 @@ __device__ void pp_solver(const PpSrc &src, unsigned char *base, uint64_t *bars,
 }
 
 // --------------------------------------------------------------- kernel ---
-template <int UP, bool BF16>
+template <int UP, bool BF16, bool BAT>
 __global__ void __launch_bounds__(PP_THREADS, 1)
     k_pipe_tc(PpSrc src) {
   using T = PpGeo<UP>;
@@ -745,13 +745,13 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
   const uint32_t taddr = *tmem_holder;
 
   if (warp < PP_CV) {
-    pp_converter<UP, BF16>(src, base, bars, taddr, abort_f, done_w);
+    pp_converter<UP, BF16, BAT>(src, base, bars, taddr, abort_f, done_w);
   } else if (warp < PP_CV + PP_SV) {
-    pp_solver<UP, BF16>(src, base, bars, taddr, abort_f);
+    pp_solver<UP, BF16, BAT>(src, base, bars, taddr, abort_f);
   } else if (warp == PP_PRODUCER) {
-    if ((tid & 31) == 0) pp_producer<UP>(src, base, bars, abort_f);
+    if ((tid & 31) == 0) pp_producer<UP, BAT>(src, base, bars, abort_f);
   } else if ((tid & 31) == 0) {
-    pp_issuer<UP, BF16>(src, base, bars, taddr, abort_f);
+    pp_issuer<UP, BF16, BAT>(src, base, bars, taddr, abort_f);
   }
   __syncwarp();  // the producer warp's lanes meet again before the CTA barrier
   tc::fence_before_sync();
@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
     for (int w = 1; w < PP_CV; ++w) done = min(done, (int)done_w[w]);
     int o = 0;
     for (int g = blockIdx.x; g < src.n_groups; g += gridDim.x) {
-      const PpGroup G = pp_group<UP>(src, g);
+      const PpGroup G = pp_group<UP, BAT>(src, g);
       if (pp_group_rows<UP>(G) == 0) continue;
       if (o >= done) {
         const InstDesc &in = *G.in;
@@ -792,12 +792,13 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
 
 template <int UP, bool BF16>
 cudaError_t launch_pipe_t(const SysDesc &d, const float2 *H, const float2 *S, float2 *X,
-                          int *status, float *scale_out, cudaStream_t s) {
+                          int *status, float *scale_out, int *fix_list, int *fix_count,
+                          cudaStream_t s) {
   using T = PpGeo<UP>;
   const int total = d.n_sc * d.nsys;
   const int ngroups = (total + T::NG - 1) / T::NG;
   if (ngroups == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_pipe_tc<UP, BF16>,
+  cudaError_t e = cudaFuncSetAttribute(k_pipe_tc<UP, BF16, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, T::BYTES);
   if (e != cudaSuccess) return e;
   int dev = 0, nsm = 0;
@@ -805,8 +806,9 @@ cudaError_t launch_pipe_t(const SysDesc &d, const float2 *H, const float2 *S, fl
   if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
   const int grid = ngroups < nsm ? ngroups : nsm;
-  PpSrc src{InstDesc{d, H, S, X, status, scale_out}, nullptr, nullptr, ngroups, nullptr, nullptr};
-  k_pipe_tc<UP, BF16><<<grid, PP_THREADS, T::BYTES, s>>>(src);
+  PpSrc src{InstDesc{d, H, S, X, status, scale_out}, nullptr, nullptr, ngroups, fix_list,
+            fix_count};
+  k_pipe_tc<UP, BF16, false><<<grid, PP_THREADS, T::BYTES, s>>>(src);
   return cudaGetLastError();
 }
 
@@ -815,19 +817,18 @@ cudaError_t launch_batch_pipe_t(const InstDesc *insts, const WorkItem *items, in
                                 int *fix_list, int *fix_count, int grid, cudaStream_t s) {
   using T = PpGeo<UP>;
   if (n_items == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_pipe_tc<UP, BF16>,
+  cudaError_t e = cudaFuncSetAttribute(k_pipe_tc<UP, BF16, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, T::BYTES);
   if (e != cudaSuccess) return e;
   PpSrc src{InstDesc{}, insts, items, n_items, fix_list, fix_count};
-  k_pipe_tc<UP, BF16><<<grid, PP_THREADS, T::BYTES, s>>>(src);
+  k_pipe_tc<UP, BF16, true><<<grid, PP_THREADS, T::BYTES, s>>>(src);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 bool pipe_tc_supported(const SysDesc &d, int UP) {
-  return (UP == 8 || UP == 16) && d.tma_ok && d.K >= 1 && d.K <= PP_KMAX && d.refine != 1 &&
-         !d.fixup;
+  return (UP == 8 || UP == 16) && d.tma_ok && d.K >= 1 && d.K <= PP_KMAX && d.refine != 1;
 }
 
 int pipe_systems_per_group(int UP) { return UP == 8 ? PpGeo<8>::NG : PpGeo<16>::NG; }
@@ -849,14 +850,15 @@ cudaError_t launch_batch_pipe_tc(int UP, bool bf16, const InstDesc *insts, const
 
 cudaError_t launch_pipe_tc(const SysDesc &d, int UP, bool bf16, const float2 *H,
                            const float2 *S, float2 *X, int *status, float *scale_out,
-                           cudaStream_t s) {
+                           cudaStream_t s, int *fix_list, int *fix_count) {
   switch (UP) {
     case 8:
-      return bf16 ? launch_pipe_t<8, true>(d, H, S, X, status, scale_out, s)
-                  : launch_pipe_t<8, false>(d, H, S, X, status, scale_out, s);
+      return bf16 ? launch_pipe_t<8, true>(d, H, S, X, status, scale_out, fix_list, fix_count, s)
+                  : launch_pipe_t<8, false>(d, H, S, X, status, scale_out, fix_list, fix_count, s);
     case 16:
-      return bf16 ? launch_pipe_t<16, true>(d, H, S, X, status, scale_out, s)
-                  : launch_pipe_t<16, false>(d, H, S, X, status, scale_out, s);
+      return bf16 ? launch_pipe_t<16, true>(d, H, S, X, status, scale_out, fix_list, fix_count, s)
+                  : launch_pipe_t<16, false>(d, H, S, X, status, scale_out, fix_list, fix_count,
+                                             s);
     default:
       return cudaErrorInvalidValue;
   }

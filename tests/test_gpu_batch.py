@@ -67,14 +67,21 @@ def test_batch_matches_oracle_and_single_plans():
         tol = TOL_FP32 if prec == "fp32" else TOL_LP
         err = rel_err_per_sc(Xg, ref["X"])
         assert err.max() <= tol, (i, p.U, p.B, p.C, p.mode, prec, err.max())
-        # the single-plan path runs the same device code
+        # the single-plan path runs the same device code -- except for more
+        # than 32 users in reduced precision, where the batch runs the split
+        # form (Gram, solve with one row per thread, apply): the same
+        # arithmetic per element, sums in another order
         pl = dp.Plan(p.U, p.B, p.C, p.n_sc, p.K, mode=p.mode,
                      prec=prec, N0=p.N0, tau=p.tau,
                      cluster_sizes=p.cluster_sizes)
         X1 = torch.empty_like(Xs[i])
         pl.precode(Hs[i], Ss[i], X1)
         torch.cuda.synchronize()
-        assert torch.equal(X1, Xs[i]), i
+        if prec != "fp32" and p.U > 32:
+            d = rel_err_per_sc(X1.cpu().numpy(), Xs[i].cpu().numpy().astype(np.complex128))
+            assert d.max() <= 1e-5, (i, d.max())
+        else:
+            assert torch.equal(X1, Xs[i]), i
     b.close()
 
 
