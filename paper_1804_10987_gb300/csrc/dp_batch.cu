@@ -203,7 +203,7 @@ cudaError_t enqueue_bucket(dp_batch *b, int k, cudaStream_t s) {
     for (int ph = 1; ph <= 3 && e == cudaSuccess; ++ph)
       e = (ph == 2 && dp::row_solve_supported(bk.UP))
               ? dp::launch_solve_rows(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, q + 1, bk.ws,
-                                      std::min(b->n_sm, n), s)
+                                      b->n_sm, s)
               : dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, q + ph - 1,
                                     bk.Kmax, grid, s, nullptr, nullptr, ph, bk.ws);
     return e;

@@ -126,7 +126,7 @@ cudaError_t launch_batch_pipe_tc(int UP, bool bf16, const InstDesc *insts, const
 // and queue conventions as launch_batch_tc's phase 2.
 bool row_solve_supported(int UP);
 cudaError_t launch_solve_rows(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
-                              int n_items, int *queue, const SplitWs &ws, int grid,
+                              int n_items, int *queue, const SplitWs &ws, int n_sm,
                               cudaStream_t s);
 
 // FD-WF clusters with B_c < U (and B_c <= 32) in the B_c x B_c form:

@@ -185,10 +185,12 @@ def torch_channel(n_sc: int, B: int, U: int, channel: str, gen, device,
     h = torch.complex(torch.randn((n_sc, B, U), generator=gen, device=device) * sd,
                       torch.randn((n_sc, B, U), generator=gen, device=device) * sd)
     if channel == "kron":
-        LB = torch.linalg.cholesky(torch.tensor(exp_corr(B, r_B), dtype=torch.float32,
-                                                device=device)).to(torch.complex64)
-        LU = torch.linalg.cholesky(torch.tensor(exp_corr(U, r_U), dtype=torch.float32,
-                                                device=device)).to(torch.complex64)
+        # the factors on the host (numpy), so that the draw needs no device
+        # linear-algebra library
+        LB = torch.tensor(np.linalg.cholesky(exp_corr(B, r_B)), dtype=torch.complex64,
+                          device=device)
+        LU = torch.tensor(np.linalg.cholesky(exp_corr(U, r_U)), dtype=torch.complex64,
+                          device=device)
         h = LB @ h @ LU.T
     return h.contiguous()
 
