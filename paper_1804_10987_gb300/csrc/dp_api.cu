@@ -22,6 +22,7 @@ struct dp_plan {
   int *d_status = nullptr;  // [n_sc * nsys]: status of every system of the last call
   int *d_fix = nullptr;     // reduced precision: groups to redo (list, then its count)
   int n_fix = 0;            // entries of the list
+  int n_sm = 0;             // SMs of the plan's device
   int nsys = 1;
   int dbg_stall_us = 0;  // failure injection for tests (dp_debug_stall)
   // FD-WF clusters with B_c < U (<= 32) run the B_c x B_c form
@@ -258,7 +259,7 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
   }
   if (cudaMalloc(&p->d_off, sizeof(int) * (d.C + 1)) != cudaSuccess ||
       cudaMalloc(&p->d_status, sizeof(int) * status_len(d)) != cudaSuccess ||
-      (p->n_fix && cudaMalloc(&p->d_fix, sizeof(int) * (p->n_fix + 1)) != cudaSuccess)) {
+      (p->n_fix && cudaMalloc(&p->d_fix, sizeof(int) * (p->n_fix + 2)) != cudaSuccess)) {
     cudaGetLastError();
     cudaFree(p->d_off);
     cudaFree(p->d_status);
@@ -266,9 +267,13 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
     delete p;
     return DP_ERR_OOM;
   }
+  int dev = 0;
   if (cudaMemcpy(p->d_off, p->off.data(), sizeof(int) * (d.C + 1), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
-      cudaMemset(p->d_status, 0, sizeof(int) * status_len(d)) != cudaSuccess) {
+      cudaMemset(p->d_status, 0, sizeof(int) * status_len(d)) != cudaSuccess ||
+      (p->d_fix && cudaMemset(p->d_fix + p->n_fix, 0, 2 * sizeof(int)) != cudaSuccess) ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(p->d_off);
     cudaFree(p->d_status);
@@ -368,19 +373,14 @@ cudaError_t precode_range(dp_plan *p, const float2 *h, const float2 *sy, float2 
   if (p->d.prec != DP_FP32 && dp::pipe_tc_supported(sd, p->UP)) {
     const bool fix = sd.refine == 2 && p->d_fix;
     int *list = fix ? p->d_fix : nullptr, *count = fix ? p->d_fix + p->n_fix : nullptr;
-    if (fix) e = cudaMemsetAsync(count, 0, sizeof(int), p->stream);
-    if (e == cudaSuccess)
-      e = dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
-                             p->stream, list, count);
+    e = dp::launch_pipe_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,
+                           p->stream, list, count);
     if (e != cudaSuccess || !fix) return e;
     // automatic precision escalation: the group kernel redoes the groups the
-    // warp-specialized kernel listed (with an empty list its CTAs leave at once)
-    int dev = 0, nsm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-      return e;
+    // warp-specialized kernel listed (with an empty list its CTAs leave at
+    // once), and empties the list for the next call
     return dp::launch_fixup_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, list, count,
-                               nsm, p->stream);
+                               p->n_sm, p->stream);
   }
   if (p->d.prec != DP_FP32)
     return dp::launch_fused_tc(sd, p->UP, p->d.prec == DP_BF16, h, sy, x, status, nullptr,

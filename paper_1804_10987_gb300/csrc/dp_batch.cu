@@ -190,14 +190,14 @@ cudaError_t enqueue_bucket(dp_batch *b, int k, cudaStream_t s) {
   const int n = (int)bk.items.size();
   const int grid = std::max(1, std::min<int>(bk.blocks * b->n_sm, n));
   if (bk.family == FAM_PIPE) {
-    if (bk.fix && (e = cudaMemsetAsync(bk.d_fix + n, 0, sizeof(int), s)) != cudaSuccess) return e;
+    // the list's count is the bucket's third counter (zeroed above)
     e = dp::launch_batch_pipe_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n,
-                                 bk.fix ? bk.d_fix : nullptr, bk.fix ? bk.d_fix + n : nullptr,
+                                 bk.fix ? bk.d_fix : nullptr, bk.fix ? q + 2 : nullptr,
                                  std::min(b->n_sm, n), s);
     if (e != cudaSuccess || !bk.fix) return e;
     // automatic refinement: the group kernel redoes the listed groups
     return dp::launch_batch_tc(bk.UP, bk.bf16, b->d_insts, bk.d_items, n, q, bk.Kmax,
-                               std::max(1, bk.fix_blocks * b->n_sm), s, bk.d_fix, bk.d_fix + n);
+                               std::max(1, bk.fix_blocks * b->n_sm), s, bk.d_fix, q + 2);
   }
   if (bk.family == FAM_TC && bk.split) {
     for (int ph = 1; ph <= 3 && e == cudaSuccess; ++ph)
@@ -545,7 +545,7 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
     if (bk.fix) {
       bk.fix_blocks = dp::tc_max_blocks_per_sm(bk.UP, bk.bf16, bk.Kmax);
       if (bk.fix_blocks < 1 ||
-          cudaMalloc(&bk.d_fix, sizeof(int) * (bk.items.size() + 1)) != cudaSuccess) {
+          cudaMalloc(&bk.d_fix, sizeof(int) * bk.items.size()) != cudaSuccess) {
         cudaGetLastError();
         free_batch(b);
         return bk.fix_blocks < 1 ? DP_ERR_UNSUPPORTED : DP_ERR_OOM;

@@ -133,8 +133,10 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t *bar, uint32_t parity,
                                              const volatile int *abort_f) {
   for (uint32_t i = 0; i < kWaitIters; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_f) return false;
-    if (i >= kSpinBeforeSleep) __nanosleep(64);
+    if (i >= kSpinBeforeSleep) {  // the flag is read once the wait is a long one
+      if (*abort_f) return false;
+      __nanosleep(64);
+    }
   }
   return false;
 }

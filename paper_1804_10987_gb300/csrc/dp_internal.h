@@ -62,7 +62,7 @@ struct TcOps {
                            const int *fix_count, int phase, const SplitWs &ws);
   static int blocks(bool bf16, int Kmax);
   static cudaError_t fixup(const SysDesc &d, bool bf16, const float2 *H, const float2 *S,
-                           float2 *X, int *status, const int *fix_list, const int *fix_count,
+                           float2 *X, int *status, const int *fix_list, int *fix_count,
                            int grid, cudaStream_t s);
 };
 
@@ -103,14 +103,16 @@ int tc_max_blocks_per_sm(int UP, bool bf16, int Kmax);
 bool pipe_tc_supported(const SysDesc &d, int UP);
 // fix_list / fix_count (may be NULL): with automatic refinement the groups
 // (of tc_systems_per_group(UP) systems) holding flagged systems are appended
-// there (the count zeroed before the launch), for launch_fixup_tc.
+// there, for launch_fixup_tc: fix_count[0] the entries, fix_count[1] that
+// kernel's reader count; both zero before the first launch, and that kernel
+// leaves them zero again.
 cudaError_t launch_pipe_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
                            float2 *X, int *status, float *scale_out, cudaStream_t s,
                            int *fix_list = nullptr, int *fix_count = nullptr);
 // The group kernel over those listed groups (grid CTAs; nothing when the
-// list is empty).
+// list is empty), which then empties the list.
 cudaError_t launch_fixup_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
-                            float2 *X, int *status, const int *fix_list, const int *fix_count,
+                            float2 *X, int *status, const int *fix_list, int *fix_count,
                             int grid, cudaStream_t s);
 // The same kernel over a batch bucket's work items (groups of up to
 // pipe_systems_per_group(UP) systems of one instance), one CTA per SM (grid);

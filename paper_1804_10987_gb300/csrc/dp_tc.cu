@@ -52,7 +52,7 @@ cudaError_t launch_fused_tc(const SysDesc &d, int UP, bool bf16, const float2 *H
 }
 
 cudaError_t launch_fixup_tc(const SysDesc &d, int UP, bool bf16, const float2 *H, const float2 *S,
-                            float2 *X, int *status, const int *fix_list, const int *fix_count,
+                            float2 *X, int *status, const int *fix_list, int *fix_count,
                             int grid, cudaStream_t s) {
   DP_TC_DISPATCH(UP, O::fixup(d, bf16, H, S, X, status, fix_list, fix_count, grid, s),
                  cudaErrorInvalidValue);

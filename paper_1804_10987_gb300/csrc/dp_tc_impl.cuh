@@ -800,10 +800,18 @@ __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
 // leaves at once.
 template <int UP, bool BF16>
 __global__ void __launch_bounds__(NT, TcGeo<UP>::MIN_BLOCKS)
-    k_fixup_tc(InstDesc in, const int *__restrict__ fix_list, const int *__restrict__ fix_count,
-               int Kmax) {
+    k_fixup_tc(InstDesc in, const int *__restrict__ fix_list, int *fix_count, int Kmax) {
   extern __shared__ unsigned char smem_raw[];
   const int n = *fix_count;
+  // the list is emptied for the next call by the last CTA to have read it
+  // (fix_count[1] counts the readers), so the caller needs no reset
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(fix_count + 1, 1) == (int)gridDim.x - 1) {
+      fix_count[0] = 0;
+      fix_count[1] = 0;
+    }
+  }
   if ((int)blockIdx.x >= n) return;
   const int total = in.d.n_sc * in.d.nsys;
   TcCtx cx;
@@ -906,7 +914,7 @@ cudaError_t launch_tc_u(const SysDesc &d, bool bf16, const float2 *H, const floa
 
 template <int UP, bool BF16>
 cudaError_t launch_fixup_tc_t(const SysDesc &d, const float2 *H, const float2 *S, float2 *X,
-                              int *status, const int *fix_list, const int *fix_count, int grid,
+                              int *status, const int *fix_list, int *fix_count, int grid,
                               cudaStream_t s) {
   const TcSmem L = tc_smem_layout<UP>(d.K);
   cudaError_t e = cudaFuncSetAttribute(k_fixup_tc<UP, BF16>,
@@ -962,7 +970,7 @@ cudaError_t TcOps<UP>::batch(bool bf16, const InstDesc *insts, const WorkItem *i
 }
 template <int UP>
 cudaError_t TcOps<UP>::fixup(const SysDesc &d, bool bf16, const float2 *H, const float2 *S,
-                             float2 *X, int *status, const int *fix_list, const int *fix_count,
+                             float2 *X, int *status, const int *fix_list, int *fix_count,
                              int grid, cudaStream_t s) {
   return bf16 ? launch_fixup_tc_t<UP, true>(d, H, S, X, status, fix_list, fix_count, grid, s)
               : launch_fixup_tc_t<UP, false>(d, H, S, X, status, fix_list, fix_count, grid, s);

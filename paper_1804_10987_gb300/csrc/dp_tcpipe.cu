@@ -139,16 +139,23 @@ __device__ __forceinline__ PpGroup pp_group(const PpSrc &src, int g) {
   return PpGroup{&src.in0, g * PpGeo<UP>::NG, min(PpGeo<UP>::NG, total - g * PpGeo<UP>::NG)};
 }
 
+// The instance of a group: a single plan's reads its descriptor straight from
+// the kernel parameters.
+template <bool BAT>
+__device__ __forceinline__ const InstDesc &pp_in(const PpSrc &src, const PpGroup &G) {
+  if constexpr (BAT) return *G.in;
+  else return src.in0;
+}
+
 // A system of a group: subcarrier, first antenna, antennas; live = exists and
 // is not left to the B_c x B_c kernel.
 struct PpSys {
   int n, lo, nr;
   bool live;
 };
-__device__ __forceinline__ PpSys pp_sys(const PpGroup &G, int s) {
+__device__ __forceinline__ PpSys pp_sys(const SysDesc &d, const PpGroup &G, int s) {
   PpSys r{0, 0, 0, false};
   if (s < G.nact) {
-    const SysDesc &d = G.in->d;
     const int sys = G.sys0 + s;
     r.n = sys / d.nsys;
     int lo, hi;
@@ -164,10 +171,10 @@ __device__ __forceinline__ PpSys pp_sys(const PpGroup &G, int s) {
 // Largest antenna count over the live systems of a group (0: nothing to do;
 // every role skips such a group).
 template <int UP>
-__device__ int pp_group_rows(const PpGroup &G) {
+__device__ int pp_group_rows(const SysDesc &d, const PpGroup &G) {
   int m = 0;
   for (int s = 0; s < PpGeo<UP>::NG; ++s) {
-    const PpSys y = pp_sys(G, s);
+    const PpSys y = pp_sys(d, G, s);
     if (y.live) m = max(m, y.nr);
   }
   return m;
@@ -192,15 +199,16 @@ __device__ void pp_producer(const PpSrc &src, unsigned char *base, uint64_t *bar
   for (int g = blockIdx.x; ok; g += gridDim.x) {
     const bool have = g < src.n_groups;
     const PpGroup G = have ? pp_group<UP, BAT>(src, g) : PpGroup{nullptr, 0, 0};
-    const int rows = have ? pp_group_rows<UP>(G) : 0;
+    const int rows = have ? pp_group_rows<UP>(pp_in<BAT>(src, G).d, G) : 0;
     if (have && rows == 0) continue;
     if (have) {
-      const SysDesc &d = G.in->d;
+      const InstDesc &gi = pp_in<BAT>(src, G);
+      const SysDesc &d = gi.d;
       const size_t rowb = (size_t)d.U * 8;
       for (int c = 0; c * PP_GCH < rows && ok; ++c) {
         uint32_t bytes = 0;
         for (int s = 0; s < T::NG; ++s) {
-          const PpSys y = pp_sys(G, s);
+          const PpSys y = pp_sys(d, G, s);
           const int r = y.live ? min(PP_GCH, y.nr - c * PP_GCH) : 0;
           if (r > 0) bytes += (uint32_t)(r * rowb);
         }
@@ -208,11 +216,11 @@ __device__ void pp_producer(const PpSrc &src, unsigned char *base, uint64_t *bar
         if (!dst) break;
         const uint64_t *bar = &bars[B_RAWFULL + use % PP_NRAW];
         for (int s = 0; s < T::NG; ++s) {
-          const PpSys y = pp_sys(G, s);
+          const PpSys y = pp_sys(d, G, s);
           const int r = y.live ? min(PP_GCH, y.nr - c * PP_GCH) : 0;
           if (r > 0)
             tma_load_1d(dst + s * PP_GCH * rowb,
-                        G.in->H + ((size_t)y.n * d.B + y.lo + c * PP_GCH) * d.U,
+                        gi.H + ((size_t)y.n * d.B + y.lo + c * PP_GCH) * d.U,
                         (uint32_t)(r * rowb), const_cast<uint64_t *>(bar));
         }
         ++use;
@@ -220,16 +228,17 @@ __device__ void pp_producer(const PpSrc &src, unsigned char *base, uint64_t *bar
     }
     if (prev >= 0 && ok) {
       const PpGroup P = pp_group<UP, BAT>(src, prev);
-      const SysDesc &d = P.in->d;
+      const InstDesc &pi = pp_in<BAT>(src, P);
+      const SysDesc &d = pi.d;
       const size_t rowb = (size_t)d.U * 8;
       for (int s = 0; s < T::NG && ok; ++s) {
-        const PpSys y = pp_sys(P, s);
+        const PpSys y = pp_sys(d, P, s);
         if (!y.live) continue;
         for (int m0 = 0; m0 < y.nr && ok; m0 += PP_MT) {
           const int r = min(PP_MT, y.nr - m0);
           unsigned char *dst = stage((uint32_t)(r * rowb));
           if (!dst) break;
-          tma_load_1d(dst, P.in->H + ((size_t)y.n * d.B + y.lo + m0) * d.U, (uint32_t)(r * rowb),
+          tma_load_1d(dst, pi.H + ((size_t)y.n * d.B + y.lo + m0) * d.U, (uint32_t)(r * rowb),
                       &bars[B_RAWFULL + use % PP_NRAW]);
           ++use;
         }
@@ -317,16 +326,17 @@ __device__ void pp_converter(const PpSrc &src, unsigned char *base, uint64_t *ba
   for (int g = blockIdx.x; run; g += gridDim.x) {
     const bool have = g < src.n_groups;
     const PpGroup G = have ? pp_group<UP, BAT>(src, g) : PpGroup{nullptr, 0, 0};
-    const int rows = have ? pp_group_rows<UP>(G) : 0;
+    const int rows = have ? pp_group_rows<UP>(pp_in<BAT>(src, G).d, G) : 0;
     if (have && rows == 0) continue;
 
     // ---- Gram of group g (ordinal o): chunks of 64 antennas ------------------
     if (have) {
-      const int U = G.in->d.U;
+      const SysDesc &gd = pp_in<BAT>(src, G).d;
+      const int U = gd.U;
       // the thread's items all belong to one system (NTH is a multiple of
       // NG * UP), whose rows it keeps in registers
       const int s_mine = (tid / UP) % NG;
-      const PpSys y_mine = pp_sys(G, s_mine);
+      const PpSys y_mine = pp_sys(gd, G, s_mine);
       const int nr_mine = y_mine.live ? y_mine.nr : 0;
       const int nch = (rows + PP_GCH - 1) / PP_GCH;
       for (int c = 0; c < nch && run; ++c) {
@@ -373,7 +383,8 @@ __device__ void pp_converter(const PpSrc &src, unsigned char *base, uint64_t *ba
     // ---- apply of the previous group (ordinal o - 1) -------------------------
     if (prev >= 0) {
       const PpGroup P = pp_group<UP, BAT>(src, prev);
-      const int U = P.in->d.U, K = P.in->d.K, B = P.in->d.B;
+      const InstDesc &pi = pp_in<BAT>(src, P);
+      const int U = pi.d.U, K = pi.d.K, B = pi.d.B;
       const int po = o - 1, zb = po & 1;
       bool w = !*abort_f && mbar_wait_ab(&bars[B_ZREADY + zb], (po >> 1) & 1, abort_f);
       if (!__all_sync(FULL, w)) {
@@ -383,9 +394,9 @@ __device__ void pp_converter(const PpSrc &src, unsigned char *base, uint64_t *ba
       PpPend pend{nullptr, 0, 0, 0, 0, 0.f, false};
       bool has_pend = false;
       for (int s = 0; s < NG && run; ++s) {
-        const PpSys y = pp_sys(P, s);
+        const PpSys y = pp_sys(pi.d, P, s);
         if (!y.live) continue;
-        float2 *Xn = P.in->X + (size_t)y.n * K * B + y.lo;
+        float2 *Xn = pi.X + (size_t)y.n * K * B + y.lo;
         const bool good = st_i[zb * NG + s] == ST_OK;
         float os = 0.f;
         const uint32_t bb = bsys_i & 1;
@@ -525,7 +536,7 @@ __device__ void pp_issuer(const PpSrc &src, unsigned char *base, uint64_t *bars,
   for (int g = blockIdx.x; ok; g += gridDim.x) {
     const bool have = g < src.n_groups;
     const PpGroup G = have ? pp_group<UP, BAT>(src, g) : PpGroup{nullptr, 0, 0};
-    const int rows = have ? pp_group_rows<UP>(G) : 0;
+    const int rows = have ? pp_group_rows<UP>(pp_in<BAT>(src, G).d, G) : 0;
     if (have && rows == 0) continue;
     if (have) {
       const int nch = (rows + PP_GCH - 1) / PP_GCH;
@@ -550,7 +561,7 @@ __device__ void pp_issuer(const PpSrc &src, unsigned char *base, uint64_t *bars,
       const PpGroup P = pp_group<UP, BAT>(src, prev);
       const int zb = (o - 1) & 1;
       for (int s = 0; s < NG && ok; ++s) {
-        const PpSys y = pp_sys(P, s);
+        const PpSys y = pp_sys(pp_in<BAT>(src, P).d, P, s);
         if (!y.live) continue;
         const uint32_t b0 = bop_u + (bsys_i & 1) * 3 * PP_BOP;
         for (int m0 = 0; m0 < y.nr && ok; m0 += PP_MT) {
@@ -610,13 +621,13 @@ __device__ void pp_solver(const PpSrc &src, unsigned char *base, uint64_t *bars,
   int o = 0;
   for (int g = blockIdx.x; g < src.n_groups; g += gridDim.x) {
     const PpGroup G = pp_group<UP, BAT>(src, g);
-    if (pp_group_rows<UP>(G) == 0) continue;
-    const InstDesc &in = *G.in;
+    if (pp_group_rows<UP>(pp_in<BAT>(src, G).d, G) == 0) continue;
+    const InstDesc &in = pp_in<BAT>(src, G);
     const SysDesc &d = in.d;
     const int U = d.U, K = d.K;
     const float kappa = d.kappa;
     const int sys = G.sys0 + sysi, zb = o & 1;
-    const PpSys y = pp_sys(G, sysi);
+    const PpSys y = pp_sys(in.d, G, sysi);
     float2 *Sz = reinterpret_cast<float2 *>(base + T::SZ) + (size_t)(zb * NG + sysi) * PP_KMAX * UP;
     // the converters are done with this buffer's previous group (o - 2)
     bool w = !*abort_f;
@@ -763,12 +774,12 @@ __global__ void __launch_bounds__(PP_THREADS, 1)
     int o = 0;
     for (int g = blockIdx.x; g < src.n_groups; g += gridDim.x) {
       const PpGroup G = pp_group<UP, BAT>(src, g);
-      if (pp_group_rows<UP>(G) == 0) continue;
+      if (pp_group_rows<UP>(pp_in<BAT>(src, G).d, G) == 0) continue;
       if (o >= done) {
-        const InstDesc &in = *G.in;
+        const InstDesc &in = pp_in<BAT>(src, G);
         const SysDesc &d = in.d;
         for (int s = 0; s < T::NG; ++s) {
-          const PpSys y = pp_sys(G, s);
+          const PpSys y = pp_sys(d, G, s);
           if (!y.live) continue;
           float2 *Xn = in.X + (size_t)y.n * d.K * d.B + y.lo;
           for (int e = tid; e < y.nr * d.K; e += PP_THREADS) {
