@@ -56,6 +56,9 @@ KERNEL_SOURCES = {
                              "dp_common.cuh")],
     "fdsmall": [_CS + f for f in ("dp_fdsmall.cu", "dp_blocks.cuh", "dp_common.cuh")],
     "rows": [_CS + f for f in ("dp_rowsolve.cu", "dp_blocks.cuh", "dp_common.cuh")],
+    # the split form's three launches (tensor-core Gram, row solve, apply)
+    "split": [_CS + f for f in ("dp_tc_impl.cuh", "dp_quad.cuh", "dp_tc.cuh", "dp_rowsolve.cu",
+                                "dp_blocks.cuh", "dp_common.cuh")],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 PAPER_CONTEXT = ("PD-WF U=16 B=256 C=8 on 8 V100 (one per cluster), K=7: 0.607 ms per "
@@ -215,6 +218,8 @@ def sources_hash(kind):
 
 
 def kernel_kind(kernel):
+    if "k_solve_rows" in kernel and kernel.startswith("k_batch_tc"):
+        return "split"
     if kernel.startswith("k_pipe_tc"):
         return "pipe"
     if kernel.startswith(("k_batch_tc", "k_fused_tc")):
@@ -918,7 +923,10 @@ def our_arm(args):
                                "subcarriers_per_step": C2["n_sc"] * args.slots,
                                "l2": rec["l2"], "parallelism": f"replicas x{world}"},
                     "roofline": rec["roofline"], "cpu_baseline": rec.get("cpu_baseline"),
-                    "e2e": rec["e2e"], "clocks": rec["clocks"], "gpu_launches": args.steps,
+                    "e2e": rec["e2e"], "clocks": rec["clocks"],
+                    # per step: the warp-specialized kernel and the escalation
+                    # fix-up launch (automatic escalation is the default)
+                    "gpu_launches": 2 * args.steps,
                     "plain_fp32": rec["plain_fp32"],
                     "library_pipeline": rec.get("library_pipeline"),
                     "paper_context": PAPER_CONTEXT}
