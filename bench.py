@@ -95,6 +95,9 @@ def parse():
                     help="bound of the CPU oracle sample")
     ap.add_argument("--serve-requests", type=int, default=1500,
                     help="requests per arrival rate in the serving sweep")
+    ap.add_argument("--serving-knee", type=int, default=0, metavar="N",
+                    help="only this: the steady-state serving sweep with N and N/4 requests "
+                         "per rate (e.g. 20000); reports each server's knee rate; one JSON line")
     ap.add_argument("--serving-burst", type=int, default=0, metavar="N",
                     help="only this: N requests submitted at once to the solve-cached FP32 "
                          "server over the serving cells (i.i.d. channels); one JSON line")
@@ -726,6 +729,52 @@ def measure_library_pipeline(torch, H, S, N0, mode, steps, warmup, Xours):
 
 
 # ---------------------------------------------------------------- serving ----
+def serving_cells(synth, torch):
+    """The serving cells: 32 cells whose sizes follow the batched
+    configuration, two channel estimates and two symbol slots each."""
+    shapes = synth.c4_instance_shapes(32, synth.seed_for(5))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(synth.seed_for(5, 1))
+    cells = []
+    for sh in shapes:
+        Ha = synth.torch_channel(sh["n_sc"], sh["B"], sh["U"], sh["channel"], gen, "cuda")
+        Hb = synth.torch_channel(sh["n_sc"], sh["B"], sh["U"], sh["channel"], gen, "cuda")
+        Sp = [synth.torch_symbols(64, (sh["n_sc"], 14, sh["U"]), gen, "cuda") for _ in range(2)]
+        cells.append((sh, Ha, Hb, Sp))
+    return cells
+
+
+def serve_run(dp, synth, cells, prec, rate, n, max_inflight=64, cache=False):
+    """n Poisson arrivals at `rate` requests/s over the cells (each cell's
+    channel switched every 5 of its slots); the server's statistics."""
+    import numpy as np
+    N0 = synth.n0_from_snr(10.0)
+    srv = dp.Server(streams=16, max_inflight=max_inflight, arena_bytes=16 << 30,
+                    auto_release=True, cache_solve=cache)
+    ids = [srv.add_cell(dict(U=sh["U"], B=sh["B"], C=sh["C"], n_sc=sh["n_sc"], K=14,
+                             mode=sh["mode"], prec=prec, N0=N0, tau=0.125), Ha)
+           for sh, Ha, _, _ in cells]
+    g = np.random.default_rng(int(rate))
+    cell_of = g.integers(0, len(cells), n)
+    t = np.cumsum(g.exponential(1.0 / rate, n)) if rate > 0 else np.zeros(n)
+    count = np.zeros(len(cells), int)
+    S_list, H_sw = [], []
+    for c in cell_of:
+        sh, Ha, Hb, Sp = cells[c]
+        S_list.append(Sp[count[c] % 2])
+        H_sw.append((Hb if (count[c] // 5) % 2 else Ha) if count[c] % 5 == 0 else None)
+        count[c] += 1
+    # warm-up pass (kernel attributes, first launches)
+    srv.replay([ids[c] for c in cell_of[:64]], S_list[:64], np.zeros(min(64, n)))
+    srv.reset_stats()
+    srv.replay([ids[c] for c in cell_of], S_list, t, H_sw)
+    st = srv.stats()
+    srv.close()
+    st["offered_subcarriers_per_s"] = (
+        rate * float(np.mean([cells[c][0]["n_sc"] for c in cell_of])) if rate > 0 else None)
+    return st
+
+
 def measure_serving(dp, synth, torch, n_req):
     """Serving: Poisson arrivals of per-slot requests over 32 cells whose sizes
     follow the batched configuration, 14 symbols per slot, each cell's channel
@@ -733,43 +782,12 @@ def measure_serving(dp, synth, torch, n_req):
     admission by free arena memory; p50 / p99 latency and throughput per
     arrival rate, FP16 Gram cells, and the plain FP32 path one request at a
     time for comparison."""
-    import numpy as np
-    shapes = synth.c4_instance_shapes(32, synth.seed_for(5))
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(synth.seed_for(5, 1))
-    N0 = synth.n0_from_snr(10.0)
-    cells = []
-    for sh in shapes:
-        Ha = synth.torch_channel(sh["n_sc"], sh["B"], sh["U"], sh["channel"], gen, "cuda")
-        Hb = synth.torch_channel(sh["n_sc"], sh["B"], sh["U"], sh["channel"], gen, "cuda")
-        Sp = [synth.torch_symbols(64, (sh["n_sc"], 14, sh["U"]), gen, "cuda") for _ in range(2)]
-        cells.append((sh, Ha, Hb, Sp))
+    cells = serving_cells(synth, torch)
     out = {"workload": "32 cells sized as the batched configuration, K=14, channel switched "
                        "every 5 slots", "rates": []}
 
     def run(prec, rate, n, max_inflight=64, cache=False):
-        srv = dp.Server(streams=16, max_inflight=max_inflight, arena_bytes=16 << 30,
-                        auto_release=True, cache_solve=cache)
-        ids = [srv.add_cell(dict(U=sh["U"], B=sh["B"], C=sh["C"], n_sc=sh["n_sc"], K=14,
-                                 mode=sh["mode"], prec=prec, N0=N0, tau=0.125), Ha)
-               for sh, Ha, _, _ in cells]
-        g = np.random.default_rng(int(rate))
-        cell_of = g.integers(0, len(cells), n)
-        t = np.cumsum(g.exponential(1.0 / rate, n)) if rate > 0 else np.zeros(n)
-        count = np.zeros(len(cells), int)
-        S_list, H_sw = [], []
-        for c in cell_of:
-            sh, Ha, Hb, Sp = cells[c]
-            S_list.append(Sp[count[c] % 2])
-            H_sw.append((Hb if (count[c] // 5) % 2 else Ha) if count[c] % 5 == 0 else None)
-            count[c] += 1
-        # warm-up pass (kernel attributes, first launches)
-        srv.replay([ids[c] for c in cell_of[:64]], S_list[:64], np.zeros(min(64, n)))
-        srv.reset_stats()
-        srv.replay([ids[c] for c in cell_of], S_list, t, H_sw)
-        st = srv.stats()
-        srv.close()
-        return st
+        return serve_run(dp, synth, cells, prec, rate, n, max_inflight, cache)
 
     for rate in (2000, 5000, 10000, 20000, 40000):
         st = run("fp16", rate, n_req)
@@ -988,12 +1006,52 @@ def our_arm(args):
         dist.destroy_process_group()
 
 
+def serving_knee(n_long, n_short):
+    """Steady-state serving: for each arrival rate, n_short and n_long Poisson
+    requests to the uncached reduced-precision (FP16 Gram) server and to the
+    solve-cached FP32 server. A rate is sustained when the server delivers at
+    least 95 % of the offered subcarriers/s and its p99 stays flat as the run
+    grows (p99 of n_long requests within 1.5x that of n_short); the knee is
+    the highest sustained rate. One JSON line."""
+    import torch
+
+    from paper_1804_10987_gb300 import dp, synth
+    cells = serving_cells(synth, torch)
+    rates = (1000, 1500, 2000, 2500, 3000, 3500)
+    out = {"serving_knee": True, "requests": [n_short, n_long],
+           "workload": "32 cells sized as the batched configuration, K=14, channel switched "
+                       "every 5 slots", "target_p99_ms": 0.5}
+    for name, prec, cache in (("uncached_fp16", "fp16", False), ("cached_fp32", "fp32", True)):
+        recs, knee = [], None
+        for rate in rates:
+            r = {"req_per_s": rate}
+            for n in (n_short, n_long):
+                st = serve_run(dp, synth, cells, prec, rate, n, cache=cache)
+                served = st["subcarriers"] / max(st["wall_s"], 1e-9)
+                r[str(n)] = {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                             "failed": st["failed"], "subcarriers_per_s": served,
+                             "offered_subcarriers_per_s": st["offered_subcarriers_per_s"],
+                             "inflight_peak": st["inflight_peak"]}
+            lo, hi = r[str(n_short)], r[str(n_long)]
+            r["sustained"] = bool(hi["subcarriers_per_s"] >= 0.95 * hi["offered_subcarriers_per_s"]
+                                  and hi["p99_ms"] <= 1.5 * lo["p99_ms"] and hi["failed"] == 0)
+            recs.append(r)
+            if r["sustained"]:
+                knee = rate
+            elif knee is not None:
+                break  # past the knee: the queue grows with the run
+        out[name] = {"rates": recs, "knee_req_per_s": knee}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.serving_burst > 0:
         serving_burst(args.serving_burst)
+    elif args.serving_knee > 0:
+        serving_knee(args.serving_knee, max(1, args.serving_knee // 4))
     else:
         our_arm(args)
 

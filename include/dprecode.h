@@ -346,9 +346,10 @@ dp_status dp_server_reset_stats(dp_server_t s);
  * process; make that first call before any stream capture, and do not use
  * the entry point after a cudaDeviceReset of that device (the kept address
  * belongs to the old context).  The cluster offsets reach the device as
- * kernel parameters: the call copies nothing from host memory.  All calls on a device share the array and each call
- * overwrites what it reads, so calls whose work overlaps on the GPU race:
- * serialize them (one stream, or events).  host_status: NULL to return after
+ * kernel parameters: the call copies nothing from host memory.  All calls
+ * on a device share the array and each call overwrites what it reads, so
+ * calls whose work overlaps on the GPU race: serialize them (one stream, or
+ * events).  host_status: NULL to return after
  * enqueueing; otherwise the call waits for the stream and writes the
  * per-subcarrier status codes into host_status[n_sc] (host memory) and
  * returns the first failure, as dp_status_get does. */
