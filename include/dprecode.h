@@ -119,6 +119,17 @@ typedef struct {
                                 the low-precision inverse);
                                 1: the refinement step for every subcarrier;
                                 -1: neither */
+  const float *cluster_power; /* FD-WF only (NULL otherwise): host array of C
+                                 weights w_c > 0 allocating the transmit power
+                                 per cluster, rho_c^2 = rho^2 w_c / sum_c' w_c'
+                                 (Sec. III-D: sum_c rho_c^2 = rho^2; the paper's
+                                 choice rho_c^2 = rho^2 / C is w_c = 1, also what
+                                 NULL means).  Each cluster's regularizer follows
+                                 Eq. (16), kappa_c = tau U N0 / rho_c^2, and its
+                                 factor sqrt(rho_c^2 / (Es t_c)).  Copied by
+                                 dp_plan_create; DP_ERR_INVALID_ARG for another
+                                 mode or a weight that is not a positive finite
+                                 number. */
 } dp_plan_desc;
 
 typedef struct dp_plan *dp_plan_t;
@@ -336,7 +347,8 @@ dp_status dp_server_reset_stats(dp_server_t s);
  * the process exits.  No plan is
  * needed and nothing is allocated: the caller passes the description (as for
  * dp_plan_create; prec must be DP_FP32, refine 0), the stream, and the device
- * arrays H [n_sc][B][U], S [n_sc][K][U], X [n_sc][K][B] in the layouts above.
+ * arrays H [n_sc][B][U], S [n_sc][K][U], X [n_sc][K][B] in the layouts above
+ * (per-cluster power, cluster_power != NULL, returns DP_ERR_UNSUPPORTED).
  * The workspace needs, rounding each part up to 256 bytes,
  *   4 (C + 1) + 4 n_sys + 8 n_sys U^2 + 8 n_sys K U + 4 n_sys  bytes,
  * n_sys = n_sc (WF/ZF) or n_sc C (FD-WF); a larger problem returns

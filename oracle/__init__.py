@@ -54,7 +54,8 @@ class _Desc(ctypes.Structure):
                 ("n_sc", ctypes.c_int), ("K", ctypes.c_int), ("mode", ctypes.c_int),
                 ("rho2", ctypes.c_double), ("N0", ctypes.c_double),
                 ("Es", ctypes.c_double), ("tau", ctypes.c_double),
-                ("fd_form", ctypes.c_int)]
+                ("fd_form", ctypes.c_int),
+                ("cluster_power", ctypes.POINTER(ctypes.c_double))]
 
 
 def _load():
@@ -146,12 +147,15 @@ def kappa_of(mode: str, U: int, N0: float, rho2: float, C: int = 1, tau: float =
 
 def precode(H, S, cluster_sizes, mode: str = "wf", rho2: float = 1.0, N0: float = 0.1,
             Es: float = 1.0, tau: float = 0.125, fd_form: int = FORM_PAPER,
-            nthreads: int = 1, outputs=("X", "scale", "t", "t_alt", "Z", "G", "Gloc", "status")):
+            nthreads: int = 1, outputs=("X", "scale", "t", "t_alt", "Z", "G", "Gloc", "status"),
+            cluster_power=None):
     """Run the oracle over all subcarriers.  H [n_sc][B][U], S [n_sc][K][U].
 
     Returns a dict with X [n_sc][K][B], scale/t/t_alt ([n_sc] or FD [n_sc][C]),
     Z ([n_sc][K][U] or FD [n_sc][C][K][U]), G [n_sc][U][U], Gloc [C][n_sc][U][U],
-    status [n_sc] (0 ok, 1 not positive definite, 2 non-finite input)."""
+    status [n_sc] (0 ok, 1 not positive definite, 2 non-finite input).
+    cluster_power: FD-WF per-cluster weights (rho_c^2 = rho2 w_c / sum w),
+    None for the paper's equal split (Sec. III-D)."""
     H, S = _c128(H), _c128(S)
     n_sc, B, U = H.shape
     K = S.shape[1]
@@ -177,8 +181,10 @@ def precode(H, S, cluster_sizes, mode: str = "wf", rho2: float = 1.0, N0: float 
     pG = arr("G", (n_sc, U, U), np.complex128)
     pGl = arr("Gloc", (C, n_sc, U, U), np.complex128)
     pst = arr("status", (n_sc,), np.int32)
+    cp = None if cluster_power is None else np.ascontiguousarray(cluster_power, dtype=np.float64)
     d = _Desc(U, B, C, cs.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n_sc, K, m,
-              float(rho2), float(N0), float(Es), float(tau), int(fd_form))
+              float(rho2), float(N0), float(Es), float(tau), int(fd_form),
+              None if cp is None else cp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     rc = _load().orc_precode(ctypes.byref(d), _ptr(H), _ptr(S), pX, pscale, pt, pta, pZ, pG,
                              pGl, pst, int(nthreads))
     if rc != OK:

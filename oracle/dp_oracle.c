@@ -11,7 +11,8 @@
  *   Thm. 1       kappa = U N0 / rho^2, beta = sqrt(tr(Q^H Q) Es / rho^2)
  *   Lemma 1      tr(Q^H Q) = tr(A^{-1}) - kappa ||A^{-1}||_F^2
  *   Sec. III-B   z = A^{-1} s / beta, x_c = H_c^H z
- *   Sec. III-D   FD-WF: rho_c^2 = rho^2 / C, kappa_c = tau_c U N0 / rho_c^2,
+ *   Sec. III-D   FD-WF: rho_c^2 = rho^2 / C (or rho^2 w_c / sum w with
+ *                per-cluster weights), kappa_c = tau_c U N0 / rho_c^2,
  *                Q_c by the B_c x B_c inverse when B_c < U, else by the
  *                U x U one, x_c = sqrt(rho_c^2 / (tr(Q_c^H Q_c) Es)) Q_c s
  * ZF is the kappa = 0 case of the WF formulas (the paper names ZF only).
@@ -290,6 +291,11 @@ static void *worker(void *arg) {
                           &sc_v, &t_v, &td_v);
       } else {
         double rho2c = d->rho2 / C;
+        if (d->cluster_power) {
+          double wsum = 0;
+          for (int c = 0; c < C; ++c) wsum += d->cluster_power[c];
+          rho2c = d->rho2 * d->cluster_power[g] / wsum;
+        }
         double kappa = d->tau * d->U * d->N0 / rho2c;
         int lo = jb->off[g], hi = jb->off[g + 1], bc = hi - lo;
         int small = d->fd_form == ORC_FORM_BCXBC ||
@@ -359,6 +365,13 @@ int orc_precode(const orc_desc *d, const orc_cplx *H, const orc_cplx *S,
     off[c + 1] = off[c] + d->cluster_sizes[c];
   }
   if (off[d->C] != d->B) { free(off); return ORC_BAD_ARG; }
+  if (d->cluster_power) {
+    for (int c = 0; c < d->C; ++c)
+      if (d->mode != ORC_FDWF || !(d->cluster_power[c] > 0) || !isfinite(d->cluster_power[c])) {
+        free(off);
+        return ORC_BAD_ARG;
+      }
+  }
   if (nthreads < 1) nthreads = 1;
   if (nthreads > d->n_sc) nthreads = d->n_sc > 0 ? d->n_sc : 1;
   job *jobs = (job *)calloc(nthreads, sizeof(job));

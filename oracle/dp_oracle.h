@@ -55,6 +55,10 @@ typedef struct {
   int mode;                 /* ORC_ZF, ORC_WF, ORC_FDWF, ORC_MRT */
   double rho2, N0, Es, tau; /* tau: FD-WF regularization factor tau_c */
   int fd_form;              /* ORC_FORM_* */
+  const double *cluster_power; /* FD-WF: C weights w_c > 0, rho_c^2 =
+                                  rho^2 w_c / sum w (Sec. III-D: the
+                                  per-cluster powers sum to rho^2); NULL:
+                                  rho_c^2 = rho^2 / C */
 } orc_desc;
 
 /* Per-cluster Gram G_c = H_c H_c^H over antennas [lo, hi) (Sec. III-B). */

@@ -23,6 +23,7 @@ struct dp_plan {
   int *d_fix = nullptr;     // reduced precision: groups to redo (list, then its count)
   int n_fix = 0;            // entries of the list
   int n_sm = 0;             // SMs of the plan's device
+  float2 *d_ckr = nullptr;  // FD-WF with per-cluster power: (kappa_c, rho_c^2) [C]
   int nsys = 1;
   int dbg_stall_us = 0;  // failure injection for tests (dp_debug_stall)
   // FD-WF clusters with B_c < U (<= 32) run the B_c x B_c form
@@ -78,6 +79,7 @@ dp::SysDesc make_sys(const dp_plan *p, bool per_cluster, const void *H) {
   s.refine = dp::refine_mode(p->d.refine, p->d.prec == DP_FP32, p->d.mode == DP_MRT);
   s.mrt = p->d.mode == DP_MRT;
   s.dbg_stall_us = p->dbg_stall_us;
+  s.ckr = (p->d.mode == DP_FDWF && per_cluster) ? p->d_ckr : nullptr;
   return s;
 }
 
@@ -198,6 +200,10 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
       !(d.N0 >= 0.f) || !std::isfinite(d.N0) || !(d.tau >= 0.f) || !std::isfinite(d.tau))
     return DP_ERR_INVALID_ARG;
   if (!dp::refine_valid(d.refine)) return DP_ERR_INVALID_ARG;
+  std::vector<float2> ckr;  // per-cluster power (FD-WF)
+  if (!dp::cluster_power_table(d.mode == DP_FDWF, d.cluster_power, d.C, d.rho2, d.tau, d.U,
+                               d.N0, ckr))
+    return DP_ERR_INVALID_ARG;
   // The tensor-core path covers up to 64 users.
   if (d.prec != DP_FP32 && !dp::tc_supported(dp::padded_users(d.U))) return DP_ERR_UNSUPPORTED;
 
@@ -229,6 +235,7 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
   p->d = d;
   p->sizes = sizes;
   p->d.cluster_sizes = nullptr;  // the copy lives in p->sizes
+  p->d.cluster_power = nullptr;  // the table goes to p->d_ckr
   p->off.resize(d.C + 1);
   p->off[0] = 0;
   for (int c = 0; c < d.C; ++c) p->off[c + 1] = p->off[c] + sizes[c];
@@ -259,11 +266,13 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
   }
   if (cudaMalloc(&p->d_off, sizeof(int) * (d.C + 1)) != cudaSuccess ||
       cudaMalloc(&p->d_status, sizeof(int) * status_len(d)) != cudaSuccess ||
-      (p->n_fix && cudaMalloc(&p->d_fix, sizeof(int) * (p->n_fix + 2)) != cudaSuccess)) {
+      (p->n_fix && cudaMalloc(&p->d_fix, sizeof(int) * (p->n_fix + 2)) != cudaSuccess) ||
+      (!ckr.empty() && cudaMalloc(&p->d_ckr, sizeof(float2) * ckr.size()) != cudaSuccess)) {
     cudaGetLastError();
     cudaFree(p->d_off);
     cudaFree(p->d_status);
     cudaFree(p->d_fix);
+    cudaFree(p->d_ckr);
     delete p;
     return DP_ERR_OOM;
   }
@@ -272,12 +281,15 @@ dp_status dp_plan_create(const dp_plan_desc *desc, dp_stream_t stream, dp_plan_t
           cudaSuccess ||
       cudaMemset(p->d_status, 0, sizeof(int) * status_len(d)) != cudaSuccess ||
       (p->d_fix && cudaMemset(p->d_fix + p->n_fix, 0, 2 * sizeof(int)) != cudaSuccess) ||
+      (p->d_ckr && cudaMemcpy(p->d_ckr, ckr.data(), sizeof(float2) * ckr.size(),
+                              cudaMemcpyHostToDevice) != cudaSuccess) ||
       cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&p->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(p->d_off);
     cudaFree(p->d_status);
     cudaFree(p->d_fix);
+    cudaFree(p->d_ckr);
     delete p;
     return DP_ERR_CUDA;
   }
@@ -293,6 +305,7 @@ dp_status dp_plan_destroy(dp_plan_t p) {
   cudaFree(p->d_off);
   cudaFree(p->d_status);
   cudaFree(p->d_fix);
+  cudaFree(p->d_ckr);
   cudaFree(p->w_G);
   cudaFree(p->w_Z);
   cudaFree(p->w_scale);

@@ -66,6 +66,9 @@ struct Inst {
   float2 *w_G = nullptr, *w_Z = nullptr;
   float *w_scale = nullptr;
   int *d_off = nullptr;
+  // FD-WF with per-cluster power: (kappa_c, rho_c^2) per cluster
+  std::vector<float2> ckr;
+  float2 *d_ckr = nullptr;
 };
 
 bool a16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -128,6 +131,7 @@ dp::SysDesc sys_of(const Inst &in, const void *H) {
   s.skip_small = in.has_small ? 1 : 0;
   s.refine = dp::refine_mode(d.refine, d.prec == DP_FP32, d.mode == DP_MRT);
   s.mrt = d.mode == DP_MRT;
+  s.ckr = in.d_ckr;
   return s;
 }
 
@@ -172,6 +176,7 @@ void free_batch(dp_batch *b) {
     cudaFree(in.w_Z);
     cudaFree(in.w_scale);
     cudaFree(in.d_off);
+    cudaFree(in.d_ckr);
   }
   cudaFree(b->d_insts);
   cudaFree(b->d_queues);
@@ -380,11 +385,16 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
     Inst &in = b->insts[i];
     in.d = descs[i];
     dp_status st = validate(in.d, in.off);
+    if (st == DP_OK &&
+        !dp::cluster_power_table(in.d.mode == DP_FDWF, in.d.cluster_power, in.d.C, in.d.rho2,
+                                 in.d.tau, in.d.U, in.d.N0, in.ckr))
+      st = DP_ERR_INVALID_ARG;
     if (st != DP_OK) {
       delete b;
       return st;
     }
     in.d.cluster_sizes = nullptr;
+    in.d.cluster_power = nullptr;  // the table is in.ckr
     in.UP = dp::padded_users(in.d.U);
     in.nsys = in.d.mode == DP_FDWF ? in.d.C : 1;
     int maxbc = 0;
@@ -424,9 +434,13 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
   // cluster offsets and work items
   for (int i = 0; i < n && !oom; ++i) {
     Inst &in = b->insts[i];
-    oom = cudaMalloc(&in.d_off, sizeof(int) * in.off.size()) != cudaSuccess;
+    oom = cudaMalloc(&in.d_off, sizeof(int) * in.off.size()) != cudaSuccess ||
+          (!in.ckr.empty() &&
+           cudaMalloc(&in.d_ckr, sizeof(float2) * in.ckr.size()) != cudaSuccess);
     if (oom) break;
     cudaMemcpy(in.d_off, in.off.data(), sizeof(int) * in.off.size(), cudaMemcpyHostToDevice);
+    if (in.d_ckr)
+      cudaMemcpy(in.d_ckr, in.ckr.data(), sizeof(float2) * in.ckr.size(), cudaMemcpyHostToDevice);
     const int nsys_total = in.d.n_sc * in.nsys;
     if (nsys_total == 0) continue;
     if (in.has_small && in.family != FAM_STREAM) {

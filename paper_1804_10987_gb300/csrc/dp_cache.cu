@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(NT) k_cache_invert(SysDesc d, const float2 *__
   sys_rows(d, g, lo, hi);
   if (sys_is_small(d, hi - lo)) return;
   const int U = d.U;
+  const float kappa = sys_kappa(d, sys), rho2 = sys_rho2(d, sys);
   float2 *G = reinterpret_cast<float2 *>(smem_raw);
   float2 *A = G + UP * UP;
   float2 *rc = A + UP * UP;  // [2][2][UP] row / column exchange
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(NT) k_cache_invert(SysDesc d, const float2 *__
       fin = fin && cfinite(v);
     }
     G[e] = v;
-    if (i == j) v.x += d.kappa;
+    if (i == j) v.x += kappa;
     A[e] = v;
   }
   fin = __syncthreads_and(fin) != 0;
@@ -55,16 +56,16 @@ __global__ void __launch_bounds__(NT) k_cache_invert(SysDesc d, const float2 *__
     for (int i = tid; i < U; i += NT) v += G[i * UP + i].x;
     const float t = cta_sum(v, red, tid);
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-    else sc = sqrtf(d.rho2_sys / (d.Es * t));
+    else sc = sqrtf(rho2 / (d.Es * t));
     for (int e = tid; e < UP * UP; e += NT)
       A[e] = (e / UP == e % UP) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
     __syncthreads();
   } else if (st == ST_OK) {
     st = cta_gj_inverse_reg<UP>(A, U, tid, rc);
     if (st == ST_OK) {
-      const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
+      const float t = cta_trace_tgt<UP>(A, G, kappa, U, red, tid);
       if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-      else sc = sqrtf(d.rho2_sys / (d.Es * t));
+      else sc = sqrtf(rho2 / (d.Es * t));
     }
   }
   float2 *tdst = Tout + (size_t)sys * U * U;

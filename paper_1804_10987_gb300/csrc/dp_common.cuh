@@ -178,7 +178,19 @@ struct SysDesc {
   int dbg_stall_us; // failure injection (tests): the warp-specialized kernel's
                     // MMA issuer first waits this long on a flag that nothing
                     // sets, then gives up as a timed-out wait does; 0: off
+  const float2 *ckr;  // FD-WF with per-cluster power (device, nsys entries):
+                      // (kappa_c, rho_c^2) of cluster c; NULL: kappa and
+                      // rho2_sys for every system
 };
+
+// Regularizer and power of system sys (a global system index; its cluster is
+// sys % nsys).
+__device__ __forceinline__ float sys_kappa(const SysDesc &d, int sys) {
+  return d.ckr ? d.ckr[sys % d.nsys].x : d.kappa;
+}
+__device__ __forceinline__ float sys_rho2(const SysDesc &d, int sys) {
+  return d.ckr ? d.ckr[sys % d.nsys].y : d.rho2_sys;
+}
 
 // One precoding instance: its systems and its device arrays (H [n_sc][B][U],
 // S [n_sc][K][U], X [n_sc][K][B], status [n_sc * nsys], optional scale).

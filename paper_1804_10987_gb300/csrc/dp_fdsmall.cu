@@ -98,7 +98,7 @@ __device__ void fd_small_system(const InstDesc &in, int sys, float2 *ws, int lan
   for (int b = 0; b < BCP; ++b)
     if (b == a) {
       row[b].y = 0.f;
-      row[b].x += d.kappa;  // A' = G' + kappa_c I
+      row[b].x += sys_kappa(d, sys);  // A' = G' + kappa_c I
     }
 
   // 2. T' = A'^{-1} (pivot rows come from the lanes of part 0)
@@ -149,7 +149,7 @@ __device__ void fd_small_system(const InstDesc &in, int sys, float2 *ws, int lan
   float sc = 0.f;
   if (st == ST_OK) {
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-    else sc = sqrtf(d.rho2_sys / (d.Es * t));
+    else sc = sqrtf(sys_rho2(d, sys) / (d.Es * t));
   }
   __syncwarp();
   // 4. x_c = scale Q_c s, the parts summed in order

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NT) k_solve_warp(SysDesc d, const float2 *__re
   __syncwarp();
 
   float sc = 0.f;
-  const int st = warp_solve<UP>(Gw, Sw, Z + (size_t)sys * K * U, U, d.kappa, d.rho2_sys, d.Es, U,
+  const int st = warp_solve<UP>(Gw, Sw, Z + (size_t)sys * K * U, U, sys_kappa(d, sys), sys_rho2(d, sys), d.Es, U,
                                 K, lane, fin, sc, d.mrt != 0);
   if (lane == 0) {
     scale[sys] = sc;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(NT) k_solve_cta(SysDesc d, const float2 *__res
       fin = fin && cfinite(v);
     }
     G[e] = v;
-    if (i == j) v.x += d.kappa;
+    if (i == j) v.x += sys_kappa(d, sys);
     A[e] = v;
   }
   fin = __syncthreads_and(fin) != 0;
@@ -184,13 +184,13 @@ __global__ void __launch_bounds__(NT) k_solve_cta(SysDesc d, const float2 *__res
   if (st == ST_OK && d.mrt) {  // MRT: t = tr(G), z = s
     const float t = cta_mrt<UP>(G, Ss, Zs, U, K, red, tid);
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-    else sc = sqrtf(d.rho2_sys / (d.Es * t));
+    else sc = sqrtf(sys_rho2(d, sys) / (d.Es * t));
   } else {
     if (st == ST_OK) st = cta_gj_inverse<UP>(A, U, tid);
     if (st == ST_OK) {
-      const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
+      const float t = cta_trace_tgt<UP>(A, G, sys_kappa(d, sys), U, red, tid);
       if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-      else sc = sqrtf(d.rho2_sys / (d.Es * t));
+      else sc = sqrtf(sys_rho2(d, sys) / (d.Es * t));
     }
   }
   if (st == ST_OK && !d.mrt) cta_whiten<UP>(A, Ss, Zs, U, K, tid);
@@ -336,7 +336,7 @@ __device__ bool fused_system(const InstDesc &in, int sys, unsigned char *smem_ra
   for (int e = tid; e < UP * UP; e += NT) {
     float2 v = G[e];
     gfin = gfin && cfinite(v);
-    if (e / UP == e % UP) v.x += d.kappa;  // a3: A = G + kappa I
+    if (e / UP == e % UP) v.x += sys_kappa(d, sys);  // a3: A = G + kappa I
     A[e] = v;
   }
   gfin = __syncthreads_and(gfin) != 0;
@@ -347,13 +347,13 @@ __device__ bool fused_system(const InstDesc &in, int sys, unsigned char *smem_ra
   if (st == ST_OK && d.mrt) {  // MRT: t = tr(G), z = s
     const float t = cta_mrt<UP>(G, Ss, Zs, U, K, red, tid);
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-    else sc = sqrtf(d.rho2_sys / (d.Es * t));
+    else sc = sqrtf(sys_rho2(d, sys) / (d.Es * t));
   } else {
     if (st == ST_OK) st = cta_gj_inverse<UP>(A, U, tid);
     if (st == ST_OK) {
-      const float t = cta_trace_tgt<UP>(A, G, d.kappa, U, red, tid);
+      const float t = cta_trace_tgt<UP>(A, G, sys_kappa(d, sys), U, red, tid);
       if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-      else sc = sqrtf(d.rho2_sys / (d.Es * t));
+      else sc = sqrtf(sys_rho2(d, sys) / (d.Es * t));
     }
   }
   // a5 + a6: whiten, then x = scale H^H z over the resident antenna block

@@ -4,6 +4,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <vector>
+
 #include "dp_common.cuh"
 
 namespace dp {
@@ -19,6 +22,29 @@ inline int refine_mode(int refine, bool fp32, bool mrt) {
   return refine == 1 ? 1 : (refine == 0 ? 2 : 0);
 }
 inline bool refine_valid(int refine) { return refine >= -1 && refine <= 1; }
+
+// FD-WF with per-cluster power (Sec. III-D): from the weights w[0..C) the
+// table of (kappa_c, rho_c^2) per cluster, rho_c^2 = rho2 w_c / sum w and
+// kappa_c = tau U N0 / rho_c^2 (Eq. (16)).  Equal weights give the uniform
+// split rho2 / C bit for bit.  An empty table when w is NULL; false when w is
+// given for another mode or a weight is not a positive finite number.
+inline bool cluster_power_table(bool fdwf, const float *w, int C, double rho2, double tau,
+                                double U, double N0, std::vector<float2> &t) {
+  t.clear();
+  if (!w) return true;
+  if (!fdwf || C < 1) return false;
+  double sum = 0.0;
+  for (int c = 0; c < C; ++c) {
+    if (!(w[c] > 0.f) || !std::isfinite(w[c])) return false;
+    sum += w[c];
+  }
+  if (!std::isfinite(sum)) return false;
+  for (int c = 0; c < C; ++c) {
+    const double rho2c = rho2 * (double)w[c] / sum;
+    t.push_back(make_float2((float)(tau * U * N0 / rho2c), (float)rho2c));
+  }
+  return true;
+}
 
 // CTAs of `kernel` (launched with `threads` threads and `dyn_bytes` of dynamic
 // shared memory, each holding `tmem_cols` TMEM columns) that one SM holds at

@@ -77,6 +77,13 @@ extern "C" dp_status dp_precode_noalloc(const dp_plan_desc *desc, dp_stream_t st
       (d.refine != 0 && d.refine != 1))
     return DP_ERR_INVALID_ARG;
   if (d.prec != DP_FP32 || d.refine != 0) return DP_ERR_UNSUPPORTED;
+  {
+    std::vector<float2> ckr;
+    if (!dp::cluster_power_table(d.mode == DP_FDWF, d.cluster_power, d.C, d.rho2, d.tau, d.U,
+                                 d.N0, ckr))
+      return DP_ERR_INVALID_ARG;
+    if (!ckr.empty()) return DP_ERR_UNSUPPORTED;  // per-cluster power: use a plan
+  }
 
   std::vector<int> off(d.C + 1, 0);
   for (int c = 0; c < d.C; ++c) {

@@ -66,14 +66,16 @@ __device__ __forceinline__ float quad_sys_sum(float v, float *red, int tid) {
 // Zs: [NS][K][UP] (written for every live system: z, or zeros on failure);
 // st_s: in: ST_OK or the input's failure; out: the system's status; sc_s:
 // out: scale (0 on failure).  scratch: Quad<UP>::SCRATCH_BYTES of shared
-// memory; red: NT / 32 floats; Tout: if non-NULL, T = A^{-1} [NS][UP][UP]
+// memory; sd, sys0: the descriptor and the first system (for each system's
+// kappa and rho^2); red: NT / 32 floats; Tout: if non-NULL, T = A^{-1} [NS][UP][UP]
 // (rows and columns >= U undefined); sens_s: if non-NULL, out: the
 // sensitivity estimate ||G||_F ||T||_F / U of every live system (0 for MRT
 // and on failure).  Every thread of the CTA calls it.
 template <int UP>
 __device__ void quad_solve(const float2 *Gs, const float2 *Ss, float2 *Zs, int *st_s,
-                           float *sc_s, const int *skip_s, int nact, float kappa, float rho2,
-                           float Es, int U, int K, bool mrt, float lemma_max, float2 *scratch,
+                           float *sc_s, const int *skip_s, int nact, const SysDesc &sd,
+                           int sys0, float Es, int U, int K, bool mrt, float lemma_max,
+                           float2 *scratch,
                            float *red, float2 *Tout, float *sens_s, int tid) {
   using Q = Quad<UP>;
   constexpr int QW = Q::QW, QS = Q::QS, NS = Q::NS;
@@ -82,6 +84,8 @@ __device__ void quad_solve(const float2 *Gs, const float2 *Ss, float2 *Zs, int *
   const int lane = tid & 31;
   const bool row = i < UP;  // warp-uniform: 4 UP is a multiple of 32
   const bool sys_live = s < nact && !skip_s[s];
+  // this system's regularizer and power (per cluster for FD-WF)
+  const float kappa = sys_kappa(sd, sys0 + s), rho2 = sys_rho2(sd, sys0 + s);
   const bool live = sys_live && st_s[s] == ST_OK;
   const float2 *G = Gs + (size_t)s * UP * UP;
   float2 *rb = scratch + (size_t)s * 2 * Q::ROWBUF;  // [2][4][QS]

@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(RsGeo<UP>::THREADS, 1)
       group_sync<GT>(g);
       continue;
     }
-    const float kappa = d.kappa;
+    const float kappa = sys_kappa(d, sys);
     const bool mrt = d.mrt != 0;
     const float2 *Gm = ws.G + (size_t)it * UP * UP;  // Gm[n][m] = conj(G_mn)
     // symbols (zero pads) and their finiteness
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(RsGeo<UP>::THREADS, 1)
         continue;
       }
       st = st1;
-      if (st == ST_OK) sc = sqrtf(d.rho2_sys / (d.Es * t));
+      if (st == ST_OK) sc = sqrtf(sys_rho2(d, sys) / (d.Es * t));
       break;
     }
 

@@ -100,6 +100,9 @@ struct Cell {
   dp_plan_desc d;
   std::vector<int> off;
   int *d_off = nullptr;
+  // FD-WF with per-cluster power: (kappa_c, rho_c^2) per cluster, in the same
+  // allocation as d_off (after it)
+  float2 *d_ckr = nullptr;
   int UP = 8, nsys = 1, maxrows = 0;
   bool tc = false, fused = false;
   bool has_small = false, all_small = false;  // FD-WF clusters with B_c < U
@@ -191,6 +194,7 @@ dp::SysDesc sys_of(const Cell &c, const void *H) {
   s.skip_small = c.has_small ? 1 : 0;
   s.refine = dp::refine_mode(d.refine, d.prec == DP_FP32, d.mode == DP_MRT);
   s.mrt = d.mode == DP_MRT;
+  s.ckr = c.d_ckr;
   return s;
 }
 
@@ -405,8 +409,13 @@ dp_status dp_server_add_cell(dp_server_t sv, const dp_plan_desc *desc, const voi
       (d.prec != DP_FP32 && d.prec != DP_BF16 && d.prec != DP_FP16) || !dp::refine_valid(d.refine) ||
       !(d.rho2 > 0.f) || !(d.Es > 0.f) || !(d.N0 >= 0.f) || !(d.tau >= 0.f))
     return DP_ERR_INVALID_ARG;
+  std::vector<float2> ckr;
+  if (!dp::cluster_power_table(d.mode == DP_FDWF, d.cluster_power, d.C, d.rho2, d.tau, d.U,
+                               d.N0, ckr))
+    return DP_ERR_INVALID_ARG;
   Cell c;
   c.d = d;
+  c.d.cluster_power = nullptr;  // the table goes to c.d_ckr
   c.off.assign(d.C + 1, 0);
   for (int k = 0; k < d.C; ++k) {
     const int bc = d.cluster_sizes ? d.cluster_sizes[k] : (d.B % d.C ? -1 : d.B / d.C);
@@ -446,12 +455,17 @@ dp_status dp_server_add_cell(dp_server_t sv, const dp_plan_desc *desc, const voi
   c.st_bytes = sizeof(int) * (size_t)d.n_sc * c.nsys;
   if (c.x_bytes + c.st_bytes + 512 > sv->arena.bytes()) return DP_ERR_OOM;
   std::lock_guard<std::mutex> lk(sv->mu);
+  const size_t off_bytes = (sizeof(int) * c.off.size() + 15) / 16 * 16;
   if (cudaSetDevice(sv->cfg.device) != cudaSuccess ||
-      cudaMalloc(&c.d_off, sizeof(int) * c.off.size()) != cudaSuccess) {
+      cudaMalloc(&c.d_off, off_bytes + sizeof(float2) * ckr.size()) != cudaSuccess) {
     cudaGetLastError();
     return DP_ERR_OOM;
   }
   cudaMemcpy(c.d_off, c.off.data(), sizeof(int) * c.off.size(), cudaMemcpyHostToDevice);
+  if (!ckr.empty()) {
+    c.d_ckr = reinterpret_cast<float2 *>(reinterpret_cast<char *>(c.d_off) + off_bytes);
+    cudaMemcpy(c.d_ckr, ckr.data(), sizeof(float2) * ckr.size(), cudaMemcpyHostToDevice);
+  }
   c.cached = sv->cfg.cache_solve != 0 && !c.all_small;
   // the streaming FP32 form keeps G and z per cell, so its requests stay in
   // order on the cell's stream; every other form may overlap

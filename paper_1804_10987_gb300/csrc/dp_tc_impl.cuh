@@ -593,7 +593,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
     // from H itself).  The quad solve reads G in conjugate-transposed order,
     // which for U > 32 is how the TMEM readout above stored it; for U <= 32
     // the readout stored G itself, and G is Hermitian.
-    quad_solve<UP>(Gs, Ss, Zs, st_s, sc_s, sk_s, nact, d.kappa, d.rho2_sys, d.Es, U, K,
+    quad_solve<UP>(Gs, Ss, Zs, st_s, sc_s, sk_s, nact, d, sys0, d.Es, U, K,
                    d.mrt != 0, kLemmaMaxRatioLP, reinterpret_cast<float2 *>(base + L.region),
                    sc_s + NG, refine ? Gs : nullptr, d.refine == 2 ? sens_s : nullptr, tid);
   } else {
@@ -601,7 +601,8 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
     if (warp < nact) {
       float sc = 0.f, sens = 0.f;
       const int st = warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP, Zs + warp * K * UP, UP,
-                                    d.kappa, d.rho2_sys, d.Es, U, K, lane, st_s[warp] == ST_OK,
+                                    sys_kappa(d, sys0 + warp), sys_rho2(d, sys0 + warp), d.Es, U,
+                                    K, lane, st_s[warp] == ST_OK,
                                     sc, d.mrt != 0, d.refine == 2 ? &sens : nullptr);
       if (lane == 0) {
         st_s[warp] = st;
@@ -658,15 +659,16 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
     }
     __syncthreads();
     if constexpr (UP >= 24) {
-      quad_solve<UP>(Gs, Ss, Zs, st_s, sc_s, nes_s, nact, d.kappa, d.rho2_sys, d.Es, U, K,
+      quad_solve<UP>(Gs, Ss, Zs, st_s, sc_s, nes_s, nact, d, sys0, d.Es, U, K,
                      d.mrt != 0, kLemmaMaxRatio, reinterpret_cast<float2 *>(base + L.region),
                      sc_s + NG, nullptr, nullptr, tid);
     } else {
       if (warp < nact && es_s[warp]) {
         float sc = 0.f;
         const int st = warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP,
-                                      Zs + warp * K * UP, UP, d.kappa, d.rho2_sys, d.Es, U, K,
-                                      lane, true, sc, d.mrt != 0);
+                                      Zs + warp * K * UP, UP, sys_kappa(d, sys0 + warp),
+                                      sys_rho2(d, sys0 + warp), d.Es, U, K, lane, true, sc,
+                                      d.mrt != 0);
         if (lane == 0) {
           st_s[warp] = st;
           sc_s[warp] = sc;
@@ -720,8 +722,9 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
         const float2 z0 = zz[e];
         // s itself from the input (Ss holds the previous step's residual)
         float2 r = __ldg(S + ((size_t)n_s[s] * K + k) * U + u);
-        r.x -= acc.x * inv + d.kappa * z0.x;
-        r.y -= acc.y * inv + d.kappa * z0.y;
+        const float ks = sys_kappa(d, sys0 + s);
+        r.x -= acc.x * inv + ks * z0.x;
+        r.y -= acc.y * inv + ks * z0.y;
         fin = fin && cfinite(r);
         ss[e] = r;
       }
@@ -748,8 +751,9 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
     } else {
       if (warp < nact && act_s[warp]) {
         float unused;
-        warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP, Dz + warp * K * UP, UP, d.kappa,
-                       d.rho2_sys, d.Es, U, K, lane, true, unused);
+        warp_solve<UP>(Gs + warp * UP * UP, Ss + warp * K * UP, Dz + warp * K * UP, UP,
+                       sys_kappa(d, sys0 + warp), sys_rho2(d, sys0 + warp), d.Es, U, K, lane,
+                       true, unused);
       }
     }
     __syncthreads();

@@ -625,8 +625,8 @@ __device__ void pp_solver(const PpSrc &src, unsigned char *base, uint64_t *bars,
     const InstDesc &in = pp_in<BAT>(src, G);
     const SysDesc &d = in.d;
     const int U = d.U, K = d.K;
-    const float kappa = d.kappa;
     const int sys = G.sys0 + sysi, zb = o & 1;
+    const float kappa = sys_kappa(d, sys);
     const PpSys y = pp_sys(in.d, G, sysi);
     float2 *Sz = reinterpret_cast<float2 *>(base + T::SZ) + (size_t)(zb * NG + sysi) * PP_KMAX * UP;
     // the converters are done with this buffer's previous group (o - 2)
@@ -688,7 +688,7 @@ __device__ void pp_solver(const PpSrc &src, unsigned char *base, uint64_t *bars,
     __syncwarp();
     const bool finite_in = seg_all<SEG>(fin_s && fin_g, lane);
     float sc = 0.f, zm = 0.f, sens = 0.f;
-    const int st = split_solve<UP>(row, Gw, Sz, Sz, UP, kappa, d.rho2_sys, d.Es, U, K, sl,
+    const int st = split_solve<UP>(row, Gw, Sz, Sz, UP, kappa, sys_rho2(d, sys), d.Es, U, K, sl,
                                    finite_in, true, sc, zm, d.mrt != 0,
                                    d.refine == 2 ? &sens : nullptr);
     // automatic refinement: a flagged system is applied unrefined here and

@@ -40,7 +40,8 @@ class PlanDesc(ctypes.Structure):
                 ("n_sc", ctypes.c_int), ("K", ctypes.c_int),
                 ("mode", ctypes.c_int), ("prec", ctypes.c_int),
                 ("rho2", ctypes.c_float), ("N0", ctypes.c_float), ("Es", ctypes.c_float),
-                ("tau", ctypes.c_float), ("refine", ctypes.c_int)]
+                ("tau", ctypes.c_float), ("refine", ctypes.c_int),
+                ("cluster_power", ctypes.POINTER(ctypes.c_float))]
 
 
 class ServerConfig(ctypes.Structure):
@@ -172,22 +173,19 @@ class Plan:
 
     def __init__(self, U: int, B: int, C: int, n_sc: int, K: int, mode: str = "wf",
                  prec: str = "fp32", rho2: float = 1.0, N0: float = 0.1, Es: float = 1.0,
-                 tau: float = 0.125, refine: int = 0, cluster_sizes=None, stream=None):
+                 tau: float = 0.125, refine: int = 0, cluster_sizes=None, stream=None,
+                 cluster_power=None):
         import torch
         self.U, self.B, self.C, self.n_sc, self.K = int(U), int(B), int(C), int(n_sc), int(K)
         self.mode, self.prec = mode, prec
         self.rho2, self.N0, self.Es, self.tau, self.refine = rho2, N0, Es, tau, refine
         self.cluster_sizes = None if cluster_sizes is None else [int(c) for c in cluster_sizes]
+        self.cluster_power = None if cluster_power is None else [float(w) for w in cluster_power]
         self._lib = load()
-        self._cs = None
-        cs_ptr = None
-        if self.cluster_sizes is not None:
-            self._cs = (ctypes.c_int * len(self.cluster_sizes))(*self.cluster_sizes)
-            cs_ptr = ctypes.cast(self._cs, ctypes.POINTER(ctypes.c_int))
-        if mode not in MODES or prec not in PRECISIONS:
-            raise ValueError(f"mode {mode!r} / precision {prec!r} unknown")
-        d = PlanDesc(self.U, self.B, self.C, cs_ptr, self.n_sc, self.K, MODES[mode],
-                     PRECISIONS[prec], rho2, N0, Es, tau, int(refine))
+        d, self._keep = _desc(dict(U=self.U, B=self.B, C=self.C, n_sc=self.n_sc, K=self.K,
+                                   mode=mode, prec=prec, rho2=rho2, N0=N0, Es=Es, tau=tau,
+                                   refine=refine, cluster_sizes=self.cluster_sizes,
+                                   cluster_power=self.cluster_power))
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
@@ -299,7 +297,7 @@ class Plan:
 class Batch:
     """Batched uneven precoding (dp_batch_t): n instances, each described by a
     dict with the Plan keyword arguments (U, B, C, n_sc, K, mode, prec, rho2,
-    N0, Es, tau, cluster_sizes).  precode() takes per-instance lists of device
+    N0, Es, tau, refine, cluster_sizes, cluster_power).  precode() takes per-instance lists of device
     tensors in the single-plan layouts."""
 
     def __init__(self, descs, stream=None):
@@ -310,17 +308,8 @@ class Batch:
         arr = (PlanDesc * n)()
         self._keep = []
         for i, d in enumerate(self.descs):
-            cs = d.get("cluster_sizes")
-            ptr = None
-            if cs is not None:
-                c = (ctypes.c_int * len(cs))(*[int(x) for x in cs])
-                self._keep.append(c)
-                ptr = ctypes.cast(c, ctypes.POINTER(ctypes.c_int))
-            arr[i] = PlanDesc(int(d["U"]), int(d["B"]), int(d["C"]), ptr, int(d["n_sc"]),
-                              int(d["K"]), MODES[d.get("mode", "wf")],
-                              PRECISIONS[d.get("prec", "fp32")], float(d.get("rho2", 1.0)),
-                              float(d.get("N0", 0.1)), float(d.get("Es", 1.0)),
-                              float(d.get("tau", 0.125)), int(d.get("refine", 0)))
+            arr[i], keep = _desc(d)
+            self._keep.extend(keep)
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
@@ -391,16 +380,27 @@ class Batch:
 
 
 def _desc(d: dict):
-    keep = None
-    ptr = None
+    """A PlanDesc from the Plan keyword arguments as a dict, and the ctypes
+    arrays it points to (kept alive by the caller)."""
+    keep = []
+    cs_ptr = cp_ptr = None
     cs = d.get("cluster_sizes")
     if cs is not None:
-        keep = (ctypes.c_int * len(cs))(*[int(x) for x in cs])
-        ptr = ctypes.cast(keep, ctypes.POINTER(ctypes.c_int))
-    pd = PlanDesc(int(d["U"]), int(d["B"]), int(d["C"]), ptr, int(d["n_sc"]), int(d["K"]),
-                  MODES[d.get("mode", "wf")], PRECISIONS[d.get("prec", "fp32")],
-                  float(d.get("rho2", 1.0)), float(d.get("N0", 0.1)), float(d.get("Es", 1.0)),
-                  float(d.get("tau", 0.125)), 0)
+        a = (ctypes.c_int * len(cs))(*[int(x) for x in cs])
+        keep.append(a)
+        cs_ptr = ctypes.cast(a, ctypes.POINTER(ctypes.c_int))
+    cp = d.get("cluster_power")
+    if cp is not None:
+        a = (ctypes.c_float * len(cp))(*[float(x) for x in cp])
+        keep.append(a)
+        cp_ptr = ctypes.cast(a, ctypes.POINTER(ctypes.c_float))
+    mode, prec = d.get("mode", "wf"), d.get("prec", "fp32")
+    if mode not in MODES or prec not in PRECISIONS:
+        raise ValueError(f"mode {mode!r} / precision {prec!r} unknown")
+    pd = PlanDesc(int(d["U"]), int(d["B"]), int(d["C"]), cs_ptr, int(d["n_sc"]), int(d["K"]),
+                  MODES[mode], PRECISIONS[prec], float(d.get("rho2", 1.0)),
+                  float(d.get("N0", 0.1)), float(d.get("Es", 1.0)), float(d.get("tau", 0.125)),
+                  int(d.get("refine", 0)), cp_ptr)
     return pd, keep
 
 
@@ -444,8 +444,8 @@ class Server:
         _check(self._lib.dp_server_drain(self._h), "dp_server_drain")
 
     def result(self, rid: int):
-        """(X as a new torch tensor copied out of the arena, worst status)."""
-        import torch
+        """The request's worst status code (0 when every subcarrier succeeded);
+        copy_result copies its X out of the arena."""
         x = ctypes.c_void_p()
         st = ctypes.c_int()
         _check(self._lib.dp_server_result(self._h, ctypes.c_ulonglong(rid), ctypes.byref(x),

@@ -50,13 +50,17 @@ def _create(**kw):
                 tau=0.125, refine=0)
     base.update(kw)
     cs = base.pop("cs")
-    arr = None
+    cp = base.pop("cp", None)
+    arr = parr = None
     if cs is not None:
         arr = (ctypes.c_int * len(cs))(*cs)
+    if cp is not None:
+        parr = (ctypes.c_float * len(cp))(*cp)
     d = dp.PlanDesc(base["U"], base["B"], base["C"],
                     ctypes.cast(arr, ctypes.POINTER(ctypes.c_int)) if arr else None,
                     base["n_sc"], base["K"], base["mode"], base["prec"], base["rho2"],
-                    base["N0"], base["Es"], base["tau"], base["refine"])
+                    base["N0"], base["Es"], base["tau"], base["refine"],
+                    ctypes.cast(parr, ctypes.POINTER(ctypes.c_float)) if parr else None)
     h = ctypes.c_void_p()
     rc = lib.dp_plan_create(ctypes.byref(d), None, ctypes.byref(h))
     if rc == dp.OK:
@@ -75,6 +79,12 @@ def _create(**kw):
     (dict(C=2, cs=[64, 0]), dp.PARTITION),
     (dict(mode=0, U=8, B=6, C=1), dp.UNSUPPORTED),
     (dict(mode=2, N0=0.0, U=8, B=12, C=2), dp.UNSUPPORTED),
+    # per-cluster power: FD-WF only, positive finite weights
+    (dict(mode=1, cp=[1.0, 2.0]), dp.INVALID_ARG),
+    (dict(mode=2, cp=[1.0, 0.0]), dp.INVALID_ARG),
+    (dict(mode=2, cp=[1.0, -2.0]), dp.INVALID_ARG),
+    (dict(mode=2, cp=[1.0, float("inf")]), dp.INVALID_ARG),
+    (dict(mode=2, cp=[float("nan"), 1.0]), dp.INVALID_ARG),
 ])
 def test_plan_validation_on_host(kw, code):
     assert _create(**kw) == code
@@ -150,13 +160,21 @@ def test_server_null_handles():
     assert lib.dp_server_reset_stats(None) == dp.INVALID_ARG
 
 
+_KEEP = []
+
+
 def _desc(**kw):
     base = dict(U=8, B=64, C=2, n_sc=4, K=2, mode=1, prec=0, rho2=1.0, N0=0.1, Es=1.0,
-                tau=0.125, refine=0)
+                tau=0.125, refine=0, cp=None)
     base.update(kw)
+    cp = None
+    if base["cp"] is not None:
+        arr = (ctypes.c_float * len(base["cp"]))(*base["cp"])
+        _KEEP.append(arr)
+        cp = ctypes.cast(arr, ctypes.POINTER(ctypes.c_float))
     return dp.PlanDesc(base["U"], base["B"], base["C"], None, base["n_sc"], base["K"],
                        base["mode"], base["prec"], base["rho2"], base["N0"], base["Es"],
-                       base["tau"], base["refine"])
+                       base["tau"], base["refine"], cp)
 
 
 def test_batch_validation_on_host():
@@ -180,6 +198,8 @@ def test_batch_validation_on_host():
     (dict(mode=0, U=8, B=6, C=1), dp.UNSUPPORTED),
     # workspace beyond the static array: 4000 subcarriers of U = 64 need 131 MB of G
     (dict(U=64, B=128, C=1, n_sc=4000), dp.UNSUPPORTED),
+    (dict(mode=2, cp=[1.0, 3.0]), dp.UNSUPPORTED),  # per-cluster power needs a plan
+    (dict(mode=1, cp=[1.0, 3.0]), dp.INVALID_ARG),
     (dict(n_sc=0), dp.OK),  # nothing to do, nothing enqueued
     (dict(), dp.INVALID_ARG),  # a valid description with null device arrays
 ])

@@ -408,3 +408,67 @@ def test_wf_tends_to_mrt_as_noise_grows():
     for N0, tol in ((1e3, 1e-2), (1e6, 1e-5)):
         Pw, _ = precoder_matrix(H, cs, "wf", N0=N0)
         assert np.abs(Pw - Pm).max() / np.abs(Pm).max() < tol
+
+
+# --- per-cluster power allocation (Sec. III-D and its footnote) --------------------------
+
+def test_cluster_power_equal_weights_are_the_uniform_split():
+    """w_c all equal is the paper's rho_c^2 = rho^2 / C, whatever their value."""
+    U, cs = 4, [5, 3, 8]
+    H, S = random_problem(41, 3, sum(cs), U, 2)
+    ref = oracle.precode(H, S, cs, "fdwf", N0=0.2, rho2=1.1, tau=0.5)["X"]
+    for w in ([1.0, 1.0, 1.0], [2.5, 2.5, 2.5]):
+        X = oracle.precode(H, S, cs, "fdwf", N0=0.2, rho2=1.1, tau=0.5, cluster_power=w)["X"]
+        assert np.allclose(X, ref, rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("cs", [[5, 3, 8], [2, 9, 1, 4]])
+def test_cluster_power_per_cluster_constraint(cs):
+    """Es ||P_c||_F^2 = rho_c^2 = rho^2 w_c / sum w for every cluster (the
+    per-cluster constraint of Sec. III-D with unequal powers), and the total is
+    rho^2.  Clusters with B_c < U take the B_c x B_c form."""
+    U = 4
+    w = np.arange(1, len(cs) + 1, dtype=float) ** 1.5
+    H, _ = random_problem(42, 3, sum(cs), U, 1)
+    P, out = precoder_matrix(H, cs, "fdwf", N0=0.3, rho2=1.7, Es=1.0, tau=0.25,
+                             cluster_power=w)
+    off = np.cumsum([0] + cs)
+    for n in range(3):
+        assert abs(np.linalg.norm(P[n]) ** 2 - 1.7) < 1e-12
+        for c in range(len(cs)):
+            pc = P[n, off[c]:off[c + 1]]
+            assert abs(np.linalg.norm(pc) ** 2 - 1.7 * w[c] / w.sum()) < 1e-12
+
+
+@pytest.mark.parametrize("cs,U", [([6, 3, 7], 4), ([2, 3, 5], 4)])
+def test_cluster_power_equals_a_rescaled_uniform_problem(cs, U):
+    """With rho_c^2 = w_c rho^2 (sum w = 1) the local WF of cluster c has
+    kappa_c = tau U N0 / rho_c^2.  Scaling H_c by a_c = sqrt(C w_c) turns the
+    uniform problem's (H_c H_c^H + kappa_u I) into a_c^2 (H_c H_c^H + kappa_c I)
+    (kappa_u = C tau U N0 / rho^2), so the weighted precoder on H is a_c times
+    the uniform one on the rescaled channel, cluster by cluster, in both the
+    U x U and the B_c x B_c form."""
+    C = len(cs)
+    w = np.array([0.5, 0.3, 0.2])[:C]
+    H, S = random_problem(43, 4, sum(cs), U, 3)
+    kw = dict(N0=0.15, rho2=1.0, tau=0.125)
+    Xw = oracle.precode(H, S, cs, "fdwf", cluster_power=w, **kw)["X"]
+    off = np.cumsum([0] + cs)
+    a = np.sqrt(C * w)
+    Hs = H.copy()
+    for c in range(C):
+        Hs[:, off[c]:off[c + 1]] *= a[c]
+    Xu = oracle.precode(Hs, S, cs, "fdwf", **kw)["X"]
+    for c in range(C):
+        sl = slice(off[c], off[c + 1])
+        assert np.allclose(Xw[:, :, sl], a[c] * Xu[:, :, sl], rtol=1e-10, atol=1e-13)
+    # and the weighting does change the output
+    assert not np.allclose(Xw, oracle.precode(H, S, cs, "fdwf", **kw)["X"], rtol=1e-3)
+
+
+def test_cluster_power_rejects_bad_weights():
+    H, S = random_problem(44, 1, 8, 2, 1)
+    for mode, w in (("fdwf", [1.0, 0.0]), ("fdwf", [1.0, -1.0]), ("fdwf", [1.0, np.nan]),
+                    ("wf", [1.0, 1.0])):
+        with pytest.raises(ValueError):
+            oracle.precode(H, S, [4, 4], mode, cluster_power=w)
