@@ -328,7 +328,7 @@ def measure_c4(args, dp, synth, torch, rank, world, local):
     Hs, Ss, Xs = c4_inputs(torch, synth, shapes, c4_rank_seed(synth, rank))
     stream = torch.cuda.current_stream()
     b = dp.Batch(c4_descs(synth, shapes, args.prec), stream=stream)
-    b.tune(Hs, Ss, Xs, trials=2)
+    b.tune(Hs, Ss, Xs, trials=3)
     timing = 1
     try:  # per-bucket events recorded from the graph; eager launches otherwise
         b.set_timing(1)

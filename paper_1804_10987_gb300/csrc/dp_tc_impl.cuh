@@ -419,23 +419,39 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
   const uint32_t idesc = tc::idesc_f16(128, 128, BF16);
   const uint32_t tiles_u32 = smem_u32(tiles);
   uint64_t *bar_mma = bar_tma + 1;
+  // item = (antenna octet g8, system s, user u): eight coalesced 8-byte
+  // loads, Re into tile row s*2UP + u, Im into row s*2UP + UP + u.  A
+  // thread's items of chunk c + 1 are loaded into registers while chunk c is
+  // converted and its MMAs issued.
+  constexpr int ITEMS = 8 * NG * UP, IPT = (ITEMS + NT - 1) / NT;
+  float2 pre[IPT][8];
+  auto load_chunk = [&](int c) {
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+      const int item = tid + q * NT;
+      const int u = item % UP, s = (item / UP) % NG, g8 = item / (UP * NG);
+      const bool live = item < ITEMS && s < nact && u < U;
+      const int left = nr_s[s] - (c * KC + 8 * g8);
+      const float2 *src =
+          H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KC + 8 * (live ? g8 : 0)) * U + u;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        pre[q][j] = (live && j < left) ? __ldg(src + (size_t)j * U) : make_float2(0.f, 0.f);
+    }
+  };
+  if (nchunks > 0) load_chunk(0);
   for (int c = 0; c < nchunks && ok; ++c) {
     const int buf = c & 1;
     // the MMAs of chunk c - 2 read this tile
     if (c >= 2) ok = tc_wait_mma(cx, buf);
     if (!ok) break;
-    // item = (antenna octet g8, system s, user u): eight coalesced 8-byte
-    // loads, Re into tile row s*2UP + u, Im into row s*2UP + UP + u
     unsigned char *tile = tiles + buf * TILE_BYTES;
-    for (int item = tid; item < 8 * NG * UP; item += NT) {
-      const int u = item % UP, s = (item / UP) % NG, g8 = item / (UP * NG);
-      const bool live = s < nact && u < U;
-      const float2 *src = H + ((size_t)n_s[s] * d.B + lo_s[s] + c * KC + 8 * g8) * U + u;
-      const int left = nr_s[s] - (c * KC + 8 * g8);
-      float2 v[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        v[j] = (live && j < left) ? __ldg(src + (size_t)j * U) : make_float2(0.f, 0.f);
+    for (int q = 0; q < IPT; ++q) {
+      const int item = tid + q * NT;
+      if (item >= ITEMS) continue;
+      const int u = item % UP, s = (item / UP) % NG, g8 = item / (UP * NG);
+      const float2 *v = pre[q];
       uint4 re, im;
       re.x = tc::pack2<BF16>(v[0].x, v[1].x);
       re.y = tc::pack2<BF16>(v[2].x, v[3].x);
@@ -448,6 +464,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
       *reinterpret_cast<uint4 *>(tile + tc::sw128_offset(s * M2 + u, g8)) = re;
       *reinterpret_cast<uint4 *>(tile + tc::sw128_offset(s * M2 + UP + u, g8)) = im;
     }
+    if (c + 1 < nchunks) load_chunk(c + 1);
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
