@@ -159,9 +159,11 @@ __device__ __forceinline__ bool tc_wait_mma(TcCtx &cx, int buf) {
 // K-blocks of 64 (one 128-byte swizzled row), accumulated in TMEM.  Split
 // FP16 keeps ~22 bits: A = A_hi + 2^-11 A_lo, z = z_hi + z_lo, D = A_hi z_hi
 // + A_hi z_lo + A_lo (2^-11 z_hi); z is first normalized by a power of two.
-template <int UP>
+template <int UP, bool PF = false>
 __device__ bool tc_apply(TcCtx &cx, const SysDesc &d, const float2 *__restrict__ H,
                          float2 *__restrict__ X, int nact, bool ok, const int *only = nullptr) {
+  // PF: the next step's A entries are loaded while the current MMAs run (the
+  // split form's apply launch, which has the registers for it)
   using T = TcGeo<UP>;
   constexpr int NG = T::NG;
   const TcSmem &L = cx.L;
@@ -204,6 +206,27 @@ __device__ bool tc_apply(TcCtx &cx, const SysDesc &d, const float2 *__restrict__
     const float zn = ldexpf(1.f, -zexp);    // z * zn in (-1, 1)
     const float out_scale = ldexpf(sc_s[s], zexp);
     const float2 *hsys = H + ((size_t)n_s[s] * d.B + lo_s[s]) * U;
+    // The thread's A-tile entries of one step (128-antenna tile m0, 64-entry
+    // user block kb): items e = tid + NT i, row e / 8, users 4 (e % 8)..+3 of
+    // the block.  The next step's are loaded while the current one's MMAs run.
+    constexpr int AIT = 128 * 8 / NT;
+    float2 pre[AIT][4];
+    auto load_item = [&](int i, int m0, int kb) {
+      const int mrows = min(128, nr_s[s] - m0), ent = min(64, 2 * UP - 64 * kb);
+      const int e = tid + NT * i, r = e >> 3, c8 = e & 7;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int u = 32 * kb + 4 * c8 + j;
+        pre[i][j] = (8 * c8 < ent && r < mrows && u < U)
+                        ? __ldg(hsys + (size_t)(m0 + r) * U + u)
+                        : make_float2(0.f, 0.f);
+      }
+    };
+    auto load_a = [&](int m0, int kb) {
+#pragma unroll
+      for (int i = 0; i < AIT; ++i) load_item(i, m0, kb);
+    };
+    if constexpr (PF) load_a(0, 0);
     for (int q0 = 0; q0 < K && ok; q0 += 16) {
       const int nq = min(16, K - q0);
       for (int m0 = 0; m0 < nr_s[s] && ok; m0 += 128) {
@@ -246,27 +269,20 @@ __device__ bool tc_apply(TcCtx &cx, const SysDesc &d, const float2 *__restrict__
           }
           // A tiles: rows = antennas, 16-byte chunk c8 = users 4c8..4c8+3 of
           // the block; zero beyond the block's entries and the tile's rows
-          for (int e = tid; e < 128 * 8; e += NT) {
-            const int r = e >> 3, c8 = e & 7;
+#pragma unroll
+          for (int i = 0; i < AIT; ++i) {
+            if constexpr (!PF) load_item(i, m0, kb);
+            const int e = tid + NT * i, r = e >> 3, c8 = e & 7;
             uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
             if (8 * c8 < ent) {
-              float v[8];
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const int u = 32 * kb + 4 * c8 + j;
-                const float2 h = (r < mrows && u < U)
-                                     ? __ldg(hsys + (size_t)(m0 + r) * U + u)
-                                     : make_float2(0.f, 0.f);
-                v[2 * j] = h.x;
-                v[2 * j + 1] = h.y;
-              }
               uint32_t *ph = &hi.x, *pl = &lo.x;
 #pragma unroll
               for (int j = 0; j < 4; ++j) {
-                const __half2 h2 = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+                const float2 h = pre[i][j];
+                const __half2 h2 = __floats2half2_rn(h.x, h.y);
                 const float2 hf = __half22float2(h2);
-                const __half2 l2 = __floats2half2_rn((v[2 * j] - hf.x) * 0x1p11f,
-                                                     (v[2 * j + 1] - hf.y) * 0x1p11f);
+                const __half2 l2 = __floats2half2_rn((h.x - hf.x) * 0x1p11f,
+                                                     (h.y - hf.y) * 0x1p11f);
                 ph[j] = *reinterpret_cast<const uint32_t *>(&h2);
                 pl[j] = *reinterpret_cast<const uint32_t *>(&l2);
               }
@@ -274,6 +290,13 @@ __device__ bool tc_apply(TcCtx &cx, const SysDesc &d, const float2 *__restrict__
             const uint32_t off = tc::sw128_offset(r, c8);
             *reinterpret_cast<uint4 *>(a_hi + off) = hi;
             *reinterpret_cast<uint4 *>(a_lo + off) = lo;
+          }
+          // the next step's A entries: next user block, else next tile, else
+          // the first tile again for the next 16 symbols
+          if constexpr (PF) {
+            if (kb + 1 < T::KBLK) load_a(m0, kb + 1);
+            else if (m0 + 128 < nr_s[s]) load_a(m0 + 128, 0);
+            else if (q0 + 16 < K) load_a(0, 0);
           }
           fence_proxy_async_smem();
           __syncthreads();
@@ -410,7 +433,7 @@ __device__ bool tc_group(TcCtx &cx, const InstDesc &in, int sys0, int nact,
     }
     fence_proxy_async_smem();
     __syncthreads();
-    return tc_apply<UP>(cx, d, H, X, nact, true);
+    return tc_apply<UP, true>(cx, d, H, X, nact, true);
   }
   bool ok = true;
   if constexpr (PH == PH_FUSED || PH == PH_GRAM) {
