@@ -377,6 +377,7 @@ def measure_c4(args, dp, synth, torch, rank, world, local):
                 else f"k_batch_fused<{upad}>")
         buckets.append({"kernel": kern, "family": bk["family"], "systems": bk["systems"],
                         "items": bk["items"], "ctas_per_sm": bk["ctas_per_sm"],
+                        "max_ctas_per_sm": bk["max_ctas_per_sm"], "tuned_ms": bk["tuned_ms"],
                         "launch_ms_mean": mean, "alg_bytes": bk["alg_bytes"],
                         "achieved_gbs": bk["alg_bytes"] / (mean / 1e3) / 1e9,
                         "frac": bk["alg_bytes"] / (mean / 1e3) / 1e9 / peak})

@@ -230,8 +230,10 @@ dp_status dp_status_get(dp_plan_t plan, int *host_status);
  *   and alignment as above).  Asynchronous; the pointer table is copied
  *   before the call returns.
  * dp_batch_tune: autotuner.  Runs every bucket at each feasible number of
- *   CTAs per SM (trials timed runs each, after one warm-up) on the given
- *   arrays, keeps the fastest, and rebuilds the graph.  Synchronous.
+ *   CTAs per SM (trials timed runs each, after one warm-up, each run
+ *   starting with a cold L2: a temporary buffer twice the L2 size is written
+ *   first) on the given arrays, keeps the largest count within 2 % of the
+ *   fastest, and rebuilds the graph.  Synchronous.
  * dp_batch_status_get: waits, then writes the per-subcarrier status of every
  *   instance, instance after instance, into host_status (sum of n_sc entries;
  *   NULL allowed) and returns the first failure.

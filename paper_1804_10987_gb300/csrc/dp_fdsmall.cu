@@ -94,11 +94,13 @@ __device__ void fd_small_system(const InstDesc &in, int sys, float2 *ws, int lan
 #pragma unroll
     for (int b = 0; b < BCP; ++b) row[b] = make_float2(0.f, 0.f);
   }
+  // this cluster's regularizer (read where it is used: short live range)
+  const float kap = d.ckr ? __ldg(&d.ckr[g].x) : d.kappa;
 #pragma unroll
   for (int b = 0; b < BCP; ++b)
     if (b == a) {
       row[b].y = 0.f;
-      row[b].x += sys_kappa(d, sys);  // A' = G' + kappa_c I
+      row[b].x += kap;  // A' = G' + kappa_c I
     }
 
   // 2. T' = A'^{-1} (pivot rows come from the lanes of part 0)
@@ -149,7 +151,7 @@ __device__ void fd_small_system(const InstDesc &in, int sys, float2 *ws, int lan
   float sc = 0.f;
   if (st == ST_OK) {
     if (!(t > 0.f) || !isfinite(t)) st = ST_NOT_PD;
-    else sc = sqrtf(sys_rho2(d, sys) / (d.Es * t));
+    else sc = sqrtf((d.ckr ? __ldg(&d.ckr[g].y) : d.rho2_sys) / (d.Es * t));
   }
   __syncwarp();
   // 4. x_c = scale Q_c s, the parts summed in order
@@ -185,9 +187,10 @@ __global__ void __launch_bounds__(32 * FD_WARPS, BCP == 32 ? 4 : 0) k_fd_small(I
   fd_small_system<BCP>(in, sys, ws, lane);
 }
 
-// Persistent form: every warp pulls items (one system each) from the queue.
+// Persistent form: every warp pulls items (one system each) from the queue
+// (the same register cap as above for BCP = 32).
 template <int BCP>
-__global__ void __launch_bounds__(32 * FD_WARPS)
+__global__ void __launch_bounds__(32 * FD_WARPS, BCP == 32 ? 4 : 0)
     k_batch_fd_small(const InstDesc *__restrict__ insts, const WorkItem *__restrict__ items,
                      int n_items, int *__restrict__ queue, int Kmax) {
   extern __shared__ __align__(16) float2 fd_smem[];
