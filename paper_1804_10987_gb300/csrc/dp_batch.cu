@@ -542,7 +542,7 @@ dp_status dp_batch_create(const dp_plan_desc *descs, int n, dp_stream_t stream, 
                         : bk.family == FAM_FDSMALL
                               ? dp::fd_small_max_blocks_per_sm(bk.UP, bk.Kmax)
                               : dp::fused_max_blocks_per_sm(bk.UP, bk.maxrows, bk.Kmax);
-    if (bk.family == FAM_TC && bk.UP > 32 && !bk.forced_refine) {
+    if (bk.family == FAM_TC && bk.UP > 16 && !bk.forced_refine) {
       const size_t ni = bk.items.size(), ng = (size_t)dp::tc_systems_per_group(bk.UP);
       bk.split = true;
       bk.ws.kmax = bk.Kmax;

@@ -149,9 +149,10 @@ cudaError_t launch_batch_pipe_tc(int UP, bool bf16, const InstDesc *insts, const
                                  int n_items, int *fix_list, int *fix_count, int grid,
                                  cudaStream_t s);
 
-// The split form's solve phase for 40..64 padded users with one row of A per
-// thread (four systems per CTA, one CTA per SM: grid = SMs); same workspace
-// and queue conventions as launch_batch_tc's phase 2.
+// The split form's solve phase for 24..64 padded users with one row of A per
+// thread (the blocked Gauss-Jordan of dp_rowsolve.cu; n_sm: SMs of the
+// device); same workspace and queue conventions as launch_batch_tc's phase 2,
+// the queue counting systems.
 bool row_solve_supported(int UP);
 cudaError_t launch_solve_rows(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
                               int n_items, int *queue, const SplitWs &ws, int n_sm,

@@ -1,10 +1,10 @@
 // dp_rowsolve.cu -- the solve phase (steps a3-a5: Thm. 1, Lemma 1, Eq. (14))
-// of the split tensor-core form for systems of 40..64 padded users.
+// of the split tensor-core form for systems of 24..64 padded users.
 //
-// A CTA of 256 threads is four groups of 64; each group pulls work items on
-// its own and solves one system at a time.  Thread i of a group holds row i
-// of A = G + kappa I (UP complex registers; the pad block of A is the
-// identity).
+// A CTA of 256 threads is four groups of 64 threads (40..64 users) or eight
+// groups of one warp (24 or 32 users); each group pulls systems on its own
+// and solves one at a time.  Thread i of a group holds row i of
+// A = G + kappa I (UP complex registers; the pad block of A is the identity).
 //
 // The inverse is a blocked Gauss-Jordan without pivoting, 8 pivots per step
 // (every pivot an LDL^H pivot of A, checked positive and finite):
@@ -34,15 +34,18 @@ namespace {
 
 constexpr int RS_B = 8;   // pivots per block step
 constexpr int RS_KW = 4;  // symbols whitened at once
-constexpr int RS_GROUPS = 4;
-
 template <int UP>
 struct RsGeo {
-  static_assert(UP % 8 == 0 && UP > 32 && UP <= 64, "row solve: 40..64 padded users");
+  static_assert(UP % 8 == 0 && UP >= 24 && UP <= 64, "row solve: 24..64 padded users");
   static constexpr int CW = UP;                          // columns per thread (a whole row)
-  static constexpr int GT = 64;                          // threads per group
+  static constexpr int GT = UP <= 32 ? 32 : 64;          // threads per group (one per row)
   static constexpr int WARPS = GT / 32;
-  static constexpr int THREADS = RS_GROUPS * GT;
+  static constexpr int GROUPS = 256 / GT;                // systems in flight per CTA
+  static constexpr int THREADS = GROUPS * GT;
+  static constexpr int MINB = UP <= 32 ? 2 : 1;          // CTAs per SM (registers)
+  // systems per work item: the group kernel's stacking of 128 / (2 UP)
+  // systems per tile (one for more than 32 users)
+  static constexpr int NG = (128 / (2 * UP)) > 0 ? 128 / (2 * UP) : 1;
   static constexpr int RLD = UP + 2;                     // padded row of R
   static constexpr int GJW = 2 * RS_B * RLD + WARPS * RS_B * RS_B;  // two R, M^-1 per warp
   static constexpr int TS = UP + 1;                      // padded row of T (definition of t)
@@ -166,14 +169,14 @@ __device__ __forceinline__ bool row_gj(float2 (&a)[UP], int i, float2 *gj, int g
 }
 
 template <int UP>
-__global__ void __launch_bounds__(RsGeo<UP>::THREADS, 1)
+__global__ void __launch_bounds__(RsGeo<UP>::THREADS, RsGeo<UP>::MINB)
     k_solve_rows(const InstDesc *__restrict__ insts, const WorkItem *__restrict__ items,
                  int n_items, int *__restrict__ queue, SplitWs ws, float eps_lp) {
   using R = RsGeo<UP>;
   constexpr int CW = R::CW, GT = R::GT;
   extern __shared__ __align__(16) float2 rs_smem[];
-  __shared__ int item_s[RS_GROUPS];
-  __shared__ float red_s[RS_GROUPS][R::WARPS];
+  __shared__ int item_s[R::GROUPS];
+  __shared__ float red_s[R::GROUPS][R::WARPS];
   const int tid = threadIdx.x, g = tid / GT, lt = tid % GT;
   const int i = lt;  // row of A (a whole row per thread)
   const bool row = i < UP;
@@ -185,24 +188,25 @@ __global__ void __launch_bounds__(RsGeo<UP>::THREADS, 1)
   float *red = red_s[g];
 
   for (;;) {
+    // the queue counts systems: system sq of item it (NG per item)
     if (lt == 0) item_s[g] = atomicAdd(queue, 1);
     group_sync<GT>(g);
-    const int it = item_s[g];
+    const int q = item_s[g], it = q / R::NG, sq = q - it * R::NG, wi = q;
     if (it >= n_items) break;
     const WorkItem w = items[it];
     const InstDesc &in = insts[w.inst];
     const SysDesc &d = in.d;
     const int U = d.U, K = d.K;
-    const int sys = w.sys0, n = sys / d.nsys;
+    const int sys = w.sys0 + sq, n = sys / d.nsys;
     int lo, hi;
     sys_rows(d, sys - n * d.nsys, lo, hi);
-    if (w.nact < 1 || sys_is_small(d, hi - lo)) {  // the B_c x B_c kernel's system
+    if (sq >= w.nact || sys_is_small(d, hi - lo)) {  // none, or the B_c x B_c kernel's
       group_sync<GT>(g);
       continue;
     }
     const float kappa = sys_kappa(d, sys);
     const bool mrt = d.mrt != 0;
-    const float2 *Gm = ws.G + (size_t)it * UP * UP;  // Gm[n][m] = conj(G_mn)
+    const float2 *Gm = ws.G + (size_t)wi * UP * UP;  // Gm[n][m] = conj(G_mn) (or G_mn)
     // symbols (zero pads) and their finiteness
     bool fin = true;
     for (int e = lt; e < K * UP; e += GT) {
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(RsGeo<UP>::THREADS, 1)
       fin = fin && cfinite(v);
       Sg[e] = v;
     }
-    int st = ws.st[it];  // the Gram phase's verdict
+    int st = ws.st[wi];  // the Gram phase's verdict
     if (!group_all<GT>(fin, red, g, lt) && st == ST_OK) st = ST_NONFINITE;
 
     // row i of A: A_ij = conj(Gm[j][i])
@@ -306,7 +310,7 @@ __global__ void __launch_bounds__(RsGeo<UP>::THREADS, 1)
     }
 
     // whitening z_k = T s_k (MRT: z = s), straight to the workspace
-    float2 *Zw = ws.Z + (size_t)it * ws.kmax * UP;
+    float2 *Zw = ws.Z + (size_t)wi * ws.kmax * UP;
     for (int k0 = 0; k0 < K; k0 += RS_KW) {  // RS_KW symbols at once (independent sums)
       float2 acc[RS_KW];
 #pragma unroll
@@ -333,8 +337,8 @@ __global__ void __launch_bounds__(RsGeo<UP>::THREADS, 1)
       }
     }
     if (lt == 0) {
-      ws.sc[it] = sc;
-      ws.st[it] = st;
+      ws.sc[wi] = sc;
+      ws.st[wi] = st;
       in.status[sys] = st;
       if (in.scale_out) in.scale_out[sys] = st == ST_OK ? sc : 0.f;
     }
@@ -347,14 +351,14 @@ cudaError_t launch_rows_t(const InstDesc *insts, const WorkItem *items, int n_it
                           const SplitWs &ws, bool bf16, int n_sm, cudaStream_t s) {
   using R = RsGeo<UP>;
   const size_t bytes =
-      (size_t)RS_GROUPS * ((size_t)R::SCR + (size_t)(ws.kmax + RS_KW - 1) * UP) * 8;
+      (size_t)R::GROUPS * ((size_t)R::SCR + (size_t)(ws.kmax + RS_KW - 1) * UP) * 8;
   cudaError_t e = cudaFuncSetAttribute(k_solve_rows<UP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_solve_rows<UP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  const int grid = std::max(1, std::min(n_sm, n_items));  // one CTA per SM
+  const int grid = std::max(1, std::min(n_sm * R::MINB, n_items * R::NG));
   k_solve_rows<UP><<<grid, R::THREADS, bytes, s>>>(insts, items, n_items, queue, ws,
                                                    bf16 ? 0x1p-8f : 0x1p-11f);
   return cudaGetLastError();
@@ -362,12 +366,14 @@ cudaError_t launch_rows_t(const InstDesc *insts, const WorkItem *items, int n_it
 
 }  // namespace
 
-bool row_solve_supported(int UP) { return UP > 32 && UP <= 64 && UP % 8 == 0; }
+bool row_solve_supported(int UP) { return UP >= 24 && UP <= 64 && UP % 8 == 0; }
 
 cudaError_t launch_solve_rows(int UP, bool bf16, const InstDesc *insts, const WorkItem *items,
                               int n_items, int *queue, const SplitWs &ws, int n_sm,
                               cudaStream_t s) {
   switch (UP) {
+    case 24: return launch_rows_t<24>(insts, items, n_items, queue, ws, bf16, n_sm, s);
+    case 32: return launch_rows_t<32>(insts, items, n_items, queue, ws, bf16, n_sm, s);
     case 40: return launch_rows_t<40>(insts, items, n_items, queue, ws, bf16, n_sm, s);
     case 48: return launch_rows_t<48>(insts, items, n_items, queue, ws, bf16, n_sm, s);
     case 56: return launch_rows_t<56>(insts, items, n_items, queue, ws, bf16, n_sm, s);
