@@ -42,7 +42,7 @@ struct RsGeo {
   static constexpr int WARPS = GT / 32;
   static constexpr int GROUPS = 256 / GT;                // systems in flight per CTA
   static constexpr int THREADS = GROUPS * GT;
-  static constexpr int MINB = UP <= 32 ? 2 : 1;          // CTAs per SM (registers)
+  static constexpr int MINB = UP <= 24 ? 2 : 1;          // CTAs per SM (registers)
   // systems per work item: the group kernel's stacking of 128 / (2 UP)
   // systems per tile (one for more than 32 users)
   static constexpr int NG = (128 / (2 * UP)) > 0 ? 128 / (2 * UP) : 1;
