@@ -3,7 +3,7 @@ local Grams reduced to a root, z and the precoding factor broadcast back): the
 host logic on CPU with two and three gloo ranks, the three compute steps
 supplied by the FP64 oracle's routines.  The assembled output must equal the
 oracle's centralized WF of the full channel (Thm. 1) -- PD-WF is exact
-(Sec. III-B) -- up to the FP32 precoding factor the driver carries."""
+(Sec. III-B) -- up to the FP32 precoding factor the sharded precoder carries."""
 import os
 import socket
 import sys
